@@ -1,0 +1,154 @@
+/*
+ * tt.h -- C ABI of the GB300 TT-arithmetic library (libttgb.so).
+ *
+ * Operations follow the problem statements of Al Daas, Ballard, Benner,
+ * "Parallel Algorithms for Tensor Train Arithmetic" (arXiv 2011.06532):
+ *   tt_round     Alg. 2 / Alg. 6 (TT rounding)
+ *   tt_add       Sec. 3.2.1 (summation)
+ *   tt_hadamard  Sec. 3.2.2 (Hadamard product)
+ *   tt_dot       Sec. 3.2.3, Eq. innerprodsum (inner product)
+ *   tt_norm      Sec. 3.2.4 (norm through orthonormalization)
+ *
+ * Tensor layout.  A TT tensor X has N >= 1 cores; core n (0-based) is an
+ * R[n] x I[n] x R[n+1] array with R[0] = R[N] = 1 (Sec. 2.1).  Entry (a, i, b)
+ * of core n is element a + R[n] * (i + I[n] * b) of that core's buffer: the
+ * "vec-oriented" order of Sec. 3.1, in which the horizontal unfolding H
+ * (R[n] x I[n]R[n+1]) and the vertical unfolding V (R[n]I[n] x R[n+1]) of
+ * Sec. 2.2 are both column-major.  Core buffers live in device memory of the
+ * current CUDA device.
+ *
+ * Element type.  dtype TT_F64: every step computes in FP64.  dtype TT_F32:
+ * core streams and the per-slab Householder work run in FP32 while the small
+ * factors (triangular-factor reduction trees, SVDs, rank choice, norm) stay in
+ * FP64; the result is stored in FP32.
+ *
+ * Ownership.  The library never allocates memory.  Inputs are borrowed and
+ * never modified.  Outputs are caller-owned device buffers.  Routines that need
+ * scratch space take a caller-owned device workspace whose size the matching
+ * *_workspace_size query returns; the workspace must stay untouched until the
+ * work queued on the stream has finished.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ * queued on it.  tt_round, tt_dot and tt_norm synchronize the stream before
+ * returning because they return host values (ranks, scalars).
+ *
+ * Errors.  Every routine returns a tt_status.  On TT_ERR_INVALID_ARG nothing
+ * is queued.  On any error the output contents are unspecified.  Routines are
+ * deterministic: the same input on the same GPU gives the same bits.
+ */
+#ifndef TTGB_TT_H
+#define TTGB_TT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_INVALID_ARG = 1, /* bad shape, rank, eps, dtype, null pointer or mode-size mismatch */
+  TT_ERR_WORKSPACE = 2,   /* workspace missing or smaller than the size query returned */
+  TT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  TT_ERR_NUMERICAL = 4,   /* non-finite values met, or an SVD did not converge */
+  TT_ERR_UNSUPPORTED = 6  /* a rank above TT_MAX_RANK */
+} tt_status;
+
+typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
+
+/* Largest rank (R[n]) any routine accepts. */
+#define TT_MAX_RANK 128
+
+typedef struct {
+  int32_t N;            /* number of cores, >= 1 */
+  int32_t dtype;        /* tt_dtype; all cores share it */
+  const int64_t *I;     /* host array [N], mode sizes, each >= 1 */
+  int64_t *R;           /* host array [N+1], ranks, R[0] = R[N] = 1, each >= 1;
+                           written by routines that produce this tensor */
+  void *const *cores;   /* host array [N] of device pointers, core n holds
+                           R[n] * I[n] * R[n+1] elements of dtype */
+} tt_tensor;
+
+/*
+ * Workspace bytes tt_round needs for input x (depends on N, I, R, dtype only).
+ */
+int tt_round_workspace_size(const tt_tensor *x, size_t *bytes);
+
+/*
+ * TT rounding (Alg. 2, organised as Alg. 6): a right-to-left sweep takes a
+ * tall-skinny QR of every H(X_n)^T (n = N..2) and pushes the triangular factor
+ * into core n-1; ||X|| is then the Frobenius norm of the first core; a
+ * left-to-right sweep takes, for n = 1..N-1, the SVD of the R factor of V(Y_n),
+ * keeps the smallest L_n with sum_{j > L_n} sigma_j^2 <= delta^2, delta =
+ * eps ||X|| / sqrt(N-1), writes the column-orthonormal core Q U(:, 1:L_n) and
+ * passes Sigma V^T on.  The result Y satisfies ||X - Y|| <= eps ||X|| (Alg. 2).
+ *
+ * x      input tensor (read only).
+ * eps    relative accuracy, finite and >= 0.
+ * out    out->N, out->dtype and out->I must match x; out->cores[n] must hold at
+ *        least x->R[n] * I[n] * x->R[n+1] elements (ranks never grow).  On
+ *        return out->R holds the new ranks and core n holds
+ *        out->R[n] * I[n] * out->R[n+1] elements in the layout above.
+ * workspace, workspace_bytes   device scratch of at least
+ *        tt_round_workspace_size(x) bytes (256-byte aligned).
+ * N = 1 copies the single core.  A zero tensor returns ranks all 1 and zero
+ * cores.  Synchronizes `stream` before returning.
+ */
+int tt_round(const tt_tensor *x, double eps, tt_tensor *out, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Rounds `count` independent tensors with one shared workspace, queueing them
+ * back to back on `stream` (each entry as in tt_round; eps[k] per tensor).
+ * workspace_bytes must cover the largest tt_round_workspace_size of the batch.
+ */
+int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, tt_tensor *outs, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/*
+ * Summation (Sec. 3.2.1): Z = A + B.  Interior slices are block diagonal
+ * diag(A_n(i), B_n(i)); the first core is [A_1 B_1], the last [A_N; B_N]; the
+ * ranks add (N = 1: the entrywise sum).  out->R is written by the routine;
+ * out->cores[n] must hold (Ra[n]+Rb[n]) I[n] (Ra[n+1]+Rb[n+1]) elements (with
+ * the end ranks 1).  Asynchronous.
+ */
+int tt_add(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, void *stream);
+
+/*
+ * Hadamard product (Sec. 3.2.2): Z_n(i) = A_n(i) kron B_n(i); ranks multiply.
+ * Kronecker order: row (p, q) of the slice is p * Rb + q.  out->R is written by
+ * the routine; out->cores[n] must hold Ra[n]Rb[n] I[n] Ra[n+1]Rb[n+1] elements.
+ * Asynchronous.
+ */
+int tt_hadamard(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, void *stream);
+
+/* Workspace bytes tt_dot needs for inputs a, b. */
+int tt_dot_workspace_size(const tt_tensor *a, const tt_tensor *b, size_t *bytes);
+
+/*
+ * Inner product <A, B> (Sec. 3.2.3): W_0 = 1, H(Z_n) = W_{n-1} H(A_n),
+ * W_n = V(B_n)^T V(Z_n), result = W_N.  Partial sums over slices are reduced
+ * in a fixed order in FP64.  Writes the host double *result; synchronizes.
+ */
+int tt_dot(const tt_tensor *a, const tt_tensor *b, double *result, void *workspace, size_t workspace_bytes,
+           void *stream);
+
+/* Workspace bytes tt_norm needs for input x. */
+int tt_norm_workspace_size(const tt_tensor *x, size_t *bytes);
+
+/*
+ * Norm through orthonormalization (Sec. 3.2.4, second approach): the
+ * right-to-left sweep of tt_round, then ||X|| = Frobenius norm of the first
+ * core.  Free of the cancellation of sqrt(<X, X>).  Writes the host double
+ * *result; synchronizes.
+ */
+int tt_norm(const tt_tensor *x, double *result, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Static description of a status code. */
+const char *tt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTGB_TT_H */

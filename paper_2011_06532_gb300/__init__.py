@@ -1,0 +1,228 @@
+"""TT arithmetic on one NVIDIA GB300 (sm_103a): rounding, sum, Hadamard, inner product, norm.
+
+Thin Python binding over the C ABI of include/tt.h (libttgb.so).  It only marshals
+arguments: device memory and streams come from PyTorch, every step of every
+operation runs in the library's own CUDA kernels.  There is no CPU fallback: a
+missing library or a machine without CUDA raises.
+
+A tensor is a ``DeviceTT``: mode sizes I, ranks R and a list of 1-D CUDA tensors,
+core n holding R[n]*I[n]*R[n+1] elements, entry (a, i, b) at a + R[n]*(i + I[n]*b)
+(Sec. 3.1's vec-oriented order).  float64 cores compute in FP64; float32 cores
+stream and run the per-slab Householder work in FP32 with FP64 small factors.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _native
+from ._native import build  # noqa: F401  (re-export)
+
+__all__ = ["DeviceTT", "build", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard", "tt_dot", "tt_norm",
+           "TTError", "from_host", "to_host"]
+
+_DTYPES = {torch.float64: 0, torch.float32: 1}
+
+
+class TTError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = _native.load().tt_status_string(status).decode()
+        super().__init__(f"{what}: status {status} ({msg})")
+        self.status = status
+
+
+@dataclasses.dataclass
+class DeviceTT:
+    I: List[int]
+    R: List[int]
+    cores: List[torch.Tensor]
+
+    @property
+    def N(self) -> int:
+        return len(self.I)
+
+    @property
+    def dtype(self) -> torch.dtype:
+        return self.cores[0].dtype
+
+    def core_sizes(self) -> List[int]:
+        return [self.R[n] * self.I[n] * self.R[n + 1] for n in range(self.N)]
+
+    def nbytes(self) -> int:
+        return sum(s * self.cores[0].element_size() for s in self.core_sizes())
+
+
+class _Desc:
+    """Keeps the ctypes arrays of one tt_tensor descriptor alive."""
+
+    def __init__(self, I: Sequence[int], R: Sequence[int], cores: Sequence[torch.Tensor], dtype: torch.dtype):
+        N = len(I)
+        self.I = (ctypes.c_int64 * N)(*I)
+        self.R = (ctypes.c_int64 * (N + 1))(*R)
+        self.ptrs = (ctypes.c_void_p * N)(*[c.data_ptr() for c in cores])
+        self.s = _native.TTTensor(N, _DTYPES[dtype], self.I, self.R, self.ptrs)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+    def ranks(self) -> List[int]:
+        return [int(v) for v in self.R]
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise TTError(status, what)
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _validate(x: DeviceTT):
+    if not x.cores or any(not c.is_cuda for c in x.cores):
+        raise ValueError("cores must be CUDA tensors")
+    if any(c.dtype != x.cores[0].dtype for c in x.cores) or x.cores[0].dtype not in _DTYPES:
+        raise ValueError("cores must all be float64 or all float32")
+    for n, c in enumerate(x.cores):
+        if not c.is_contiguous() or c.numel() < x.R[n] * x.I[n] * x.R[n + 1]:
+            raise ValueError(f"core {n} is too small or not contiguous")
+
+
+_ws_cache: dict = {}
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    key = (str(device),)
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        _ws_cache[key] = buf
+    return buf
+
+
+def round_workspace_size(x: DeviceTT) -> int:
+    lib = _native.load()
+    d = _Desc(x.I, x.R, x.cores, x.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_round_workspace_size(d.ref, ctypes.byref(n)), "tt_round_workspace_size")
+    return int(n.value)
+
+
+def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tensor]] = None,
+             workspace: Optional[torch.Tensor] = None) -> DeviceTT:
+    """TT rounding (Alg. 2 / Alg. 6): returns Y with ||X - Y|| <= eps ||X||."""
+    _validate(x)
+    lib = _native.load()
+    dev = x.cores[0].device
+    d = _Desc(x.I, x.R, x.cores, x.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_round_workspace_size(d.ref, ctypes.byref(n)), "tt_round_workspace_size")
+    ws = workspace if workspace is not None else _workspace(int(n.value), dev)
+    if out is None:
+        out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
+    o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
+    _check(lib.tt_round(d.ref, float(eps), o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                        _stream(stream)), "tt_round")
+    R = o.ranks()
+    cores = [out[k][: R[k] * x.I[k] * R[k + 1]] for k in range(x.N)]
+    return DeviceTT(list(x.I), R, cores)
+
+
+def tt_round_batched(xs: Sequence[DeviceTT], eps: Sequence[float], stream=None) -> List[DeviceTT]:
+    """Rounds several independent tensors with one call (shared workspace)."""
+    lib = _native.load()
+    if not xs:
+        return []
+    for x in xs:
+        _validate(x)
+    dev = xs[0].cores[0].device
+    descs = [_Desc(x.I, x.R, x.cores, x.dtype) for x in xs]
+    need = max(round_workspace_size(x) for x in xs)
+    ws = _workspace(need, dev)
+    outs = [[torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()] for x in xs]
+    odescs = [_Desc(x.I, [1] * (x.N + 1), o, x.dtype) for x, o in zip(xs, outs)]
+    arr_in = (_native.TTTensor * len(xs))(*[d.s for d in descs])
+    arr_out = (_native.TTTensor * len(xs))(*[d.s for d in odescs])
+    e = (ctypes.c_double * len(xs))(*[float(v) for v in eps])
+    _check(lib.tt_round_batched(len(xs), arr_in, e, arr_out, ctypes.c_void_p(ws.data_ptr()),
+                                ctypes.c_size_t(ws.numel()), _stream(stream)), "tt_round_batched")
+    res = []
+    for k, x in enumerate(xs):
+        R = [int(arr_out[k].R[i]) for i in range(x.N + 1)]
+        res.append(DeviceTT(list(x.I), R, [outs[k][n][: R[n] * x.I[n] * R[n + 1]] for n in range(x.N)]))
+    return res
+
+
+def tt_add(a: DeviceTT, b: DeviceTT, stream=None) -> DeviceTT:
+    """Summation (Sec. 3.2.1); ranks add."""
+    _validate(a)
+    _validate(b)
+    lib = _native.load()
+    N = a.N
+    R = [1] + [a.R[n] + b.R[n] for n in range(1, N)] + [1] if N > 1 else [1, 1]
+    dev = a.cores[0].device
+    out = [torch.empty(R[n] * a.I[n] * R[n + 1], dtype=a.dtype, device=dev) for n in range(N)]
+    da, db = _Desc(a.I, a.R, a.cores, a.dtype), _Desc(b.I, b.R, b.cores, b.dtype)
+    o = _Desc(a.I, R, out, a.dtype)
+    _check(lib.tt_add(da.ref, db.ref, o.ref, _stream(stream)), "tt_add")
+    return DeviceTT(list(a.I), o.ranks(), out)
+
+
+def tt_hadamard(a: DeviceTT, b: DeviceTT, stream=None) -> DeviceTT:
+    """Hadamard product (Sec. 3.2.2); ranks multiply."""
+    _validate(a)
+    _validate(b)
+    lib = _native.load()
+    N = a.N
+    R = [a.R[n] * b.R[n] for n in range(N + 1)]
+    dev = a.cores[0].device
+    out = [torch.empty(R[n] * a.I[n] * R[n + 1], dtype=a.dtype, device=dev) for n in range(N)]
+    da, db = _Desc(a.I, a.R, a.cores, a.dtype), _Desc(b.I, b.R, b.cores, b.dtype)
+    o = _Desc(a.I, R, out, a.dtype)
+    _check(lib.tt_hadamard(da.ref, db.ref, o.ref, _stream(stream)), "tt_hadamard")
+    return DeviceTT(list(a.I), o.ranks(), out)
+
+
+def tt_dot(a: DeviceTT, b: DeviceTT, stream=None) -> float:
+    """Inner product <A, B> (Sec. 3.2.3)."""
+    _validate(a)
+    _validate(b)
+    lib = _native.load()
+    da, db = _Desc(a.I, a.R, a.cores, a.dtype), _Desc(b.I, b.R, b.cores, b.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_dot_workspace_size(da.ref, db.ref, ctypes.byref(n)), "tt_dot_workspace_size")
+    ws = _workspace(int(n.value), a.cores[0].device)
+    res = ctypes.c_double(0.0)
+    _check(lib.tt_dot(da.ref, db.ref, ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                      _stream(stream)), "tt_dot")
+    return float(res.value)
+
+
+def tt_norm(x: DeviceTT, stream=None) -> float:
+    """Norm through orthonormalization (Sec. 3.2.4)."""
+    _validate(x)
+    lib = _native.load()
+    d = _Desc(x.I, x.R, x.cores, x.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_norm_workspace_size(d.ref, ctypes.byref(n)), "tt_norm_workspace_size")
+    ws = _workspace(int(n.value), x.cores[0].device)
+    res = ctypes.c_double(0.0)
+    _check(lib.tt_norm(d.ref, ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                       _stream(stream)), "tt_norm")
+    return float(res.value)
+
+
+def from_host(I: Sequence[int], R: Sequence[int], cores: Sequence, dtype=torch.float64, device="cuda") -> DeviceTT:
+    """Upload host cores (numpy arrays or tensors) to the GPU."""
+    dev_cores = [torch.as_tensor(c).to(device=device, dtype=dtype).contiguous() for c in cores]
+    return DeviceTT(list(map(int, I)), list(map(int, R)), dev_cores)
+
+
+def to_host(x: DeviceTT):
+    """Cores back to the host as float64 numpy arrays."""
+    return [c.detach().to("cpu", torch.float64).numpy() for c in x.cores]

@@ -1,0 +1,124 @@
+// tt_api.cu -- exported C ABI: argument validation and dispatch (see include/tt.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tt.h"
+#include "tt_engine.h"
+
+namespace {
+
+bool valid_tensor(const tt_tensor *x) {
+  if (!x || x->N < 1 || !x->I || !x->R || !x->cores) return false;
+  if (x->dtype != TT_F64 && x->dtype != TT_F32) return false;
+  if (x->R[0] != 1 || x->R[x->N] != 1) return false;
+  for (int n = 0; n < x->N; ++n) {
+    if (x->I[n] < 1 || x->R[n] < 1 || !x->cores[n]) return false;
+  }
+  return true;
+}
+
+bool ranks_supported(const tt_tensor *x) {
+  for (int n = 0; n <= x->N; ++n)
+    if (x->R[n] > TT_MAX_RANK) return false;
+  return true;
+}
+
+// out describes the same modes (N, dtype, I) with host arrays for R and cores
+bool valid_out(const tt_tensor *x, const tt_tensor *out) {
+  if (!out || out->N != x->N || out->dtype != x->dtype || !out->I || !out->R || !out->cores) return false;
+  for (int n = 0; n < x->N; ++n)
+    if (out->I[n] != x->I[n] || !out->cores[n]) return false;
+  return true;
+}
+
+bool same_modes(const tt_tensor *a, const tt_tensor *b) {
+  if (a->N != b->N || a->dtype != b->dtype) return false;
+  for (int n = 0; n < a->N; ++n)
+    if (a->I[n] != b->I[n]) return false;
+  return true;
+}
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+int tt_round_workspace_size(const tt_tensor *x, size_t *bytes) {
+  if (!valid_tensor(x) || !bytes) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (x->N == 1) {
+    *bytes = 0;
+    return TT_OK;
+  }
+  return ttgb::round_workspace(x, bytes);
+}
+
+int tt_round(const tt_tensor *x, double eps, tt_tensor *out, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!valid_tensor(x) || !valid_out(x, out) || !(eps >= 0.0) || !isfinite(eps)) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  return ttgb::round_run(x, eps, out, workspace, workspace_bytes, as_stream(stream));
+}
+
+int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, tt_tensor *outs, void *workspace,
+                     size_t workspace_bytes, void *stream) {
+  if (count < 0 || (count > 0 && (!xs || !eps || !outs))) return TT_ERR_INVALID_ARG;
+  for (int k = 0; k < count; ++k) {
+    if (!valid_tensor(&xs[k]) || !valid_out(&xs[k], &outs[k]) || !(eps[k] >= 0.0) || !isfinite(eps[k]))
+      return TT_ERR_INVALID_ARG;
+    if (!ranks_supported(&xs[k])) return TT_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < count; ++k) {
+    const int st = ttgb::round_run(&xs[k], eps[k], &outs[k], workspace, workspace_bytes, as_stream(stream));
+    if (st) return st;
+  }
+  return TT_OK;
+}
+
+int tt_add(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, void *stream) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !valid_out(a, out)) return TT_ERR_INVALID_ARG;
+  return ttgb::add_run(a, b, out, as_stream(stream));
+}
+
+int tt_hadamard(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, void *stream) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !valid_out(a, out)) return TT_ERR_INVALID_ARG;
+  return ttgb::hadamard_run(a, b, out, as_stream(stream));
+}
+
+int tt_dot_workspace_size(const tt_tensor *a, const tt_tensor *b, size_t *bytes) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !bytes) return TT_ERR_INVALID_ARG;
+  return ttgb::dot_workspace(a, b, bytes);
+}
+
+int tt_dot(const tt_tensor *a, const tt_tensor *b, double *result, void *workspace, size_t workspace_bytes,
+           void *stream) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !result) return TT_ERR_INVALID_ARG;
+  return ttgb::dot_run(a, b, result, workspace, workspace_bytes, as_stream(stream));
+}
+
+int tt_norm_workspace_size(const tt_tensor *x, size_t *bytes) {
+  if (!valid_tensor(x) || !bytes) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  return ttgb::norm_workspace(x, bytes);
+}
+
+int tt_norm(const tt_tensor *x, double *result, void *workspace, size_t workspace_bytes, void *stream) {
+  if (!valid_tensor(x) || !result) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  return ttgb::norm_run(x, result, workspace, workspace_bytes, as_stream(stream));
+}
+
+const char *tt_status_string(int status) {
+  switch (status) {
+    case TT_OK: return "ok";
+    case TT_ERR_INVALID_ARG: return "invalid argument";
+    case TT_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case TT_ERR_CUDA: return "CUDA runtime error";
+    case TT_ERR_NUMERICAL: return "non-finite values or SVD not converged";
+    case TT_ERR_UNSUPPORTED: return "unsupported size (rank above the supported maximum)";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

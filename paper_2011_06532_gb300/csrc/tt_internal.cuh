@@ -1,0 +1,175 @@
+// tt_internal.cuh -- device building blocks shared by the TT kernels.
+//
+// Tall-skinny QR on one GPU (the TSQR idea of Sec. 3.3, mapped onto CTAs):
+//   * a "leaf" CTA owns a contiguous range of mode slices of one core and runs a
+//     sequential (flat-tree) Householder QR over tiles of those slices: each tile is
+//     stacked under the CTA's running triangular factor and factored;
+//   * a G-ary tree of "node" CTAs then factors the stacked leaf triangles in the
+//     same way, level by level (one launch per level);
+//   * the orthogonal factor stays implicit (Sec. 3.5): tile and node reflectors are
+//     stored, and Q [C; 0] is applied later from the root down (TSQR-Apply-Q,
+//     Alg. 4), again as a sequence of stacked-tile reflections.
+// All of it reduces to two block-level routines on a stacked matrix
+// [Rr (k rows); tile (M rows)] with b columns: hh_factor and hh_apply.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttgb {
+
+constexpr int NT = 256;  // threads per CTA of every bulk kernel
+
+template <typename T>
+__device__ __forceinline__ T tsqrt(T x);
+template <>
+__device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Scratch a block-level routine needs in shared memory.
+template <typename T>
+struct Scratch {
+  T *red;   // NT elements
+  T *wbuf;  // >= max columns elements
+  T *sc;    // 2 elements
+};
+
+// H = I - tau u u^T with u = [1; v], v_r = V[r * ldv] for r in [r0, M), applied to the
+// stacked matrix [p (nc entries); X rows r0..M-1 (nc entries each, row stride ldx)].
+// All threads of the CTA must call it with identical arguments; nc <= NT.
+template <typename T>
+__device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, int ldx, int nc, Scratch<T> s) {
+  if (nc <= 0) return;
+  const int t = threadIdx.x;
+  const int nrow = M - r0;
+  int G = NT / nc;
+  if (G > nrow) G = nrow > 0 ? nrow : 1;
+  // partial dot products v^T X(:, c) over row groups
+  if (t < G * nc) {
+    const int g = t / nc, c = t - g * nc;
+    T acc = T(0);
+    for (int r = r0 + g; r < M; r += G) acc += V[(size_t)r * ldv] * X[(size_t)r * ldx + c];
+    s.red[g * nc + c] = acc;
+  }
+  __syncthreads();
+  for (int h = G; h > 1;) {
+    const int half = (h + 1) >> 1;
+    for (int idx = t; idx < (h - half) * nc; idx += NT) s.red[idx] += s.red[idx + half * nc];
+    h = half;
+    __syncthreads();
+  }
+  if (t < nc) {
+    const T w = tau * (p[t] + s.red[t]);
+    s.wbuf[t] = w;
+    p[t] -= w;
+  }
+  __syncthreads();
+  if (nrow > 0) {
+    // dense walk over the nrow x nc block without per-element division
+    const int dq = NT / nc, dr = NT - dq * nc;
+    int r = t / nc, c = t - (t / nc) * nc;
+    for (; r < nrow;) {
+      X[(size_t)(r0 + r) * ldx + c] -= V[(size_t)(r0 + r) * ldv] * s.wbuf[c];
+      r += dq;
+      c += dr;
+      if (c >= nc) {
+        c -= nc;
+        ++r;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Householder QR step of the stacked matrix [Rr rows 0..k-1; tile rows 0..M-1], b columns,
+// LAPACK conventions (H_j = I - tau_j u u^T, u_pivot = 1, beta = -sign(alpha) ||x||,
+// tau = 0 when the part below the pivot is zero).  Reflector j pivots on Rr row j when
+// j < k, otherwise on tile row j-k; kk = min(k + M, b) reflectors.  On return Rr rows
+// 0..k-1 hold updated R rows; tile entries (r, c) with c < k + r hold reflector entries
+// and, for r < kk - k, entries c >= k + r hold R row k + r.  tau[0..kk-1] is written.
+// Rr and tile are row-major with leading dimensions ldr, ldt.  Returns kk.
+template <typename T>
+__device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s) {
+  const int kk = min(k + M, b);
+  for (int j = 0; j < kk; ++j) {
+    const int r0 = j < k ? 0 : j - k + 1;
+    T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
+    if (threadIdx.x < 32) {
+      T ss = T(0);
+      for (int r = r0 + threadIdx.x; r < M; r += 32) {
+        const T v = tile[(size_t)r * ldt + j];
+        ss += v * v;
+      }
+      ss = warp_sum(ss);
+      if (threadIdx.x == 0) {
+        T tj = T(0), scale = T(0);
+        if (ss != T(0)) {
+          const T alpha = piv[j];
+          const T nrm = tsqrt(alpha * alpha + ss);
+          const T beta = alpha >= T(0) ? -nrm : nrm;
+          tj = (beta - alpha) / beta;
+          scale = T(1) / (alpha - beta);
+          piv[j] = beta;
+        }
+        tau[j] = tj;
+        s.sc[0] = scale;
+        s.sc[1] = tj;
+      }
+    }
+    __syncthreads();
+    const T tj = s.sc[1];
+    if (tj != T(0)) {
+      const T scale = s.sc[0];
+      for (int r = r0 + threadIdx.x; r < M; r += NT) tile[(size_t)r * ldt + j] *= scale;
+      __syncthreads();
+      reflect(tj, tile + j, ldt, r0, M, piv + j + 1, tile + j + 1, ldt, b - j - 1, s);
+    } else {
+      __syncthreads();
+    }
+  }
+  return kk;
+}
+
+// Moves the new R rows k..kk-1 produced by hh_factor from the tile into Rr (zeroing the
+// entries left of the diagonal).
+template <typename T>
+__device__ void hh_take_rows(T *Rr, int ldr, int k, int kk, const T *tile, int ldt, int b) {
+  const int n = (kk - k) * b;
+  for (int idx = threadIdx.x; idx < n; idx += NT) {
+    const int r = idx / b, c = idx - r * b;
+    Rr[(size_t)(k + r) * ldr + c] = c >= k + r ? tile[(size_t)r * ldt + c] : T(0);
+  }
+  __syncthreads();
+}
+
+// Applies the orthogonal factor of one hh_factor step, Q_t = H_0 ... H_{kk-1}, to the
+// stacked block [CR (k rows); CT (M rows)] of nc columns (row-major, leading dims ldcr,
+// ldct): reflectors are applied from kk-1 down to 0.  V / tau are the stored tile and
+// tau of that step (V row-major, ld ldv).
+template <typename T>
+__device__ void hh_apply(const T *V, int ldv, const T *tau, int k, int M, int b, T *CR, int ldcr, T *CT, int ldct,
+                         int nc, Scratch<T> s) {
+  const int kk = min(k + M, b);
+  for (int j = kk - 1; j >= 0; --j) {
+    const T tj = tau[j];
+    if (tj == T(0)) continue;
+    const int r0 = j < k ? 0 : j - k + 1;
+    T *piv = j < k ? CR + (size_t)j * ldcr : CT + (size_t)(j - k) * ldct;
+    reflect(tj, V + j, ldv, r0, M, piv, CT, ldct, nc, s);
+  }
+}
+
+__device__ __host__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Row range of leaf p when I slices are split over P leaves.
+__device__ __host__ __forceinline__ int64_t leaf_begin(int64_t I, int P, int p) { return (int64_t)p * I / P; }
+
+}  // namespace ttgb

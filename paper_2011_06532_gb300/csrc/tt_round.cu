@@ -1,0 +1,1366 @@
+// tt_round.cu -- TT rounding (Alg. 2, organised as the implicit-Q Alg. 6) and the
+// orthonormalization norm (Sec. 3.2.4) on one GPU.
+//
+// Sweep 1 (right-to-left, n = N-1..1, 0-based): for core n the leaf CTAs form the rows
+// of A = H(X_n x_3 P)^T (P = triangular factor pushed from core n+1; the push is the
+// TRMM of Alg. 6 fused into the slab load) and factor them; a tree of node CTAs reduces
+// the leaf triangles to R_n, which becomes P for core n-1.  Reflectors stay stored.
+// Sweep 2 (left-to-right, n = 0..N-2): the leaf CTAs of core n apply the stored Q_n to
+// [C_p; 0] (C = S_{n-1}^T passed down the tree; TSQR-Apply-Q, Alg. 4) to obtain slabs of
+// Y_n = S_{n-1} x_1 Q_n, transpose each slab into rows of V(Y_n) and factor those (second
+// TSQR of Alg. 6); the root factor gets an FP64 one-sided Jacobi SVD and the rank rule
+// sum_{j>L} sigma_j^2 <= delta^2; the output core is Q' [U_hat; 0] and Sigma V^T moves on.
+// The last core is S_{N-2} x_1 Q_{N-1}.
+//
+// Every size that depends on data (the new ranks) is read by the kernels from a device
+// control block, so no step needs a host synchronization; grids depend on shapes only.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "tt.h"
+#include "tt_internal.cuh"
+#include "tt_engine.h"
+
+namespace ttgb {
+
+// ------------------------------------------------------------------------------------
+// kernel argument blocks
+// ------------------------------------------------------------------------------------
+
+struct Geom {
+  int64_t I;  // slices of the core
+  int P;      // leaves
+  int Tt;     // slices per tile
+};
+
+template <typename T>
+struct S1Args {
+  const T *X;  // core n: b x I x cin
+  Geom g;
+  int b, cin, rho;   // columns (R_n), right rank of X (R_{n+1}), rows per slice (K_{n+1})
+  const double *Pm;  // rho x cin row-major (upper trapezoidal), nullptr = identity (rho == cin == 1)
+  T *refl;           // (I*rho) x b row-major
+  T *tau;            // I x b
+  double *Rleaf;     // P x b*b row-major
+  int CC;            // push chunk width
+  // shared-memory offsets (bytes)
+  int oRr, oTile, oXs, oPs, oRed, oW, oSc, oTau;
+  int ldt;
+};
+
+struct TreeArgs {
+  const double *Rin;  // children R's (b*b each) -- factor
+  double *Rout;       // node R's -- factor
+  const double *Cin;  // node C's (b*ldc each) -- apply
+  double *Cout;       // children C's -- apply
+  double *slots;      // per child: MT-row chunks of reflectors (b*b) + taus (nchunk*b)
+  int nchild, G, b, MT, nchunk;
+  int64_t I;
+  int P;
+  int lpc;               // leaves per child
+  int rho;               // rows per slice (if rho_dyn == nullptr)
+  const int *rho_dyn;    // rows per slice read from the control block
+  int ncol;              // columns of C (if ncol_dyn == nullptr)
+  const int *ncol_dyn;
+  int ldc;               // leading dimension of C blocks
+  int oA, oB, oRed, oW, oSc, oTau;  // smem offsets
+  int lda;
+};
+
+template <typename T>
+struct S2Args {
+  // mode A (core n >= 1): apply stored sweep-1 Q_n to C; mode B (core 0): push X_0
+  int mode;       // 0 = A, 1 = B, 2 = last core (mode A, write output, no V-QR)
+  Geom g;
+  // mode A
+  const T *qrefl;       // (I*K1) x b1 (sweep-1 reflectors)
+  const T *qtau;        // I x b1
+  int b1;               // columns of the sweep-1 QR (R_n)
+  int K1;               // rows per slice of the sweep-1 QR = columns of the V-QR (K_{n+1})
+  const double *Cleaf;  // per leaf: C (k_leaf x L) with leading dim ldc
+  int ldc;
+  const int *Lcur;      // &L[n]: columns of C = rows per slice of V(Y_n)
+  // mode B
+  const T *X0;          // core 0: 1 x I x cin
+  int cin;
+  const double *Pm;     // K1 x cin
+  int CC;
+  // outputs
+  T *vrefl;             // (I*L) x K1 (V-QR reflectors)
+  T *vtau;              // I x K1
+  double *Rleaf;        // P x K1*K1
+  T *out;               // last core output (L x I x 1)
+  int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv;
+  int ldq, ldv;
+};
+
+template <typename T>
+struct OutArgs {
+  Geom g;
+  const T *vrefl;
+  const T *vtau;
+  int K1;
+  const int *Lcur;      // &L[n]
+  const int *Lnext;     // &L[n+1]
+  const double *Uleaf;  // per leaf: U (k'_leaf x Lnext), leading dim ldc
+  int ldc;
+  T *out;               // output core n: L[n] x I x L[n+1]
+  int oV, oCT, oCR, oRed, oW, oSc, oTau;
+  int ldv;
+};
+
+struct SvdArgs {
+  const double *Rroot;  // K x K row-major
+  int K;                // columns
+  int64_t In;           // slices of core n
+  const int *Lcur;      // &L[n]
+  int *Lnext;           // &L[n+1]
+  int n, N;
+  double eps;
+  double *scal;         // [0] = ||X||, [1] = delta
+  double *Uhat;         // k_root x K (ld ldu)
+  double *Cnext;        // K x K (ld ldu)
+  int ldu;
+  int *status;
+};
+
+// ------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T *sm(unsigned char *base, int off) {
+  return reinterpret_cast<T *>(base + off);
+}
+
+__device__ __forceinline__ int dyn(const int *p, int v) { return p ? *p : v; }
+
+// rows of the stacked matrix owned by leaf range [l0, l1)
+__device__ __forceinline__ int64_t rows_of_leaves(int64_t I, int P, int l0, int l1, int rho) {
+  return (leaf_begin(I, P, l1) - leaf_begin(I, P, l0)) * (int64_t)rho;
+}
+
+// ------------------------------------------------------------------------------------
+// sweep 1 leaf: push + sequential Householder over tiles
+// ------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *Rr = sm<T>(smem, a.oRr), *tile = sm<T>(smem, a.oTile), *Xs = sm<T>(smem, a.oXs), *Ps = sm<T>(smem, a.oPs);
+  Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
+  T *taus = sm<T>(smem, a.oTau);
+  const int p = blockIdx.x, t = threadIdx.x;
+  const int b = a.b, rho = a.rho, cin = a.cin, ldt = a.ldt;
+  const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
+  const bool push = a.Pm != nullptr;
+  if (push)
+    for (int idx = t; idx < rho * cin; idx += NT) Ps[idx] = (T)a.Pm[idx];
+  for (int idx = t; idx < b * b; idx += NT) Rr[idx] = T(0);
+  __syncthreads();
+  int k = 0;
+  for (int64_t i0 = s0; i0 < s1; i0 += a.g.Tt) {
+    const int nt = (int)min((int64_t)a.g.Tt, s1 - i0);
+    const int M = nt * rho;
+    if (!push) {
+      // rho == cin == 1: the tile rows are the slices themselves
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int r = idx / b, c = idx - r * b;
+        tile[r * ldt + c] = a.X[(size_t)(i0 + r) * b + c];
+      }
+    } else {
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int r = idx / b, c = idx - r * b;
+        tile[r * ldt + c] = T(0);
+      }
+      for (int c0 = 0; c0 < cin; c0 += a.CC) {
+        const int cc_n = min(a.CC, cin - c0);
+        __syncthreads();
+        const int chunk = nt * b;
+        for (int idx = t; idx < cc_n * chunk; idx += NT) {
+          const int cc = idx / chunk, rem = idx - cc * chunk;
+          Xs[idx] = a.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem];
+        }
+        __syncthreads();
+        for (int idx = t; idx < M * b; idx += NT) {
+          const int r = idx / b, col = idx - r * b;
+          const int sl = r / rho, kr = r - sl * rho;
+          T acc = tile[r * ldt + col];
+          const int cstart = max(kr, c0);
+          for (int c = cstart; c < c0 + cc_n; ++c) acc += Ps[kr * cin + c] * Xs[((c - c0) * nt + sl) * b + col];
+          tile[r * ldt + col] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    const int kk = hh_factor(Rr, b, k, tile, ldt, M, b, taus, s);
+    // store reflectors and taus
+    T *dst = a.refl + (size_t)i0 * rho * b;
+    for (int idx = t; idx < M * b; idx += NT) {
+      const int r = idx / b, c = idx - r * b;
+      dst[idx] = tile[r * ldt + c];
+    }
+    for (int j = t; j < kk; j += NT) a.tau[(size_t)i0 * b + j] = taus[j];
+    hh_take_rows(Rr, b, k, kk, tile, ldt, b);
+    k = kk;
+  }
+  double *Ro = a.Rleaf + (size_t)p * b * b;
+  for (int idx = t; idx < b * b; idx += NT) Ro[idx] = (idx / b) < k ? (double)Rr[idx] : 0.0;
+}
+
+// ------------------------------------------------------------------------------------
+// tree: factor one level (children R -> node R), apply one level (node C -> children C)
+// ------------------------------------------------------------------------------------
+
+__device__ __forceinline__ int child_rows_k(const TreeArgs &a, int c, int rho) {
+  const int l0 = c * a.lpc, l1 = min(a.P, (c + 1) * a.lpc);
+  const int64_t rows = rows_of_leaves(a.I, a.P, l0, l1, rho);
+  return (int)min64(rows, a.b);
+}
+
+__global__ void __launch_bounds__(NT) k_tree_factor(TreeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *Rr = sm<double>(smem, a.oA), *tile = sm<double>(smem, a.oB);
+  Scratch<double> s{sm<double>(smem, a.oRed), sm<double>(smem, a.oW), sm<double>(smem, a.oSc)};
+  double *taus = sm<double>(smem, a.oTau);
+  const int q = blockIdx.x, t = threadIdx.x, b = a.b;
+  const int rho = dyn(a.rho_dyn, a.rho);
+  const int c0 = q * a.G, c1 = min(a.nchild, c0 + a.G);
+  int k = child_rows_k(a, c0, rho);
+  const double *R0 = a.Rin + (size_t)c0 * b * b;
+  for (int idx = t; idx < b * b; idx += NT) Rr[idx] = (idx / b) < k ? R0[idx] : 0.0;
+  __syncthreads();
+  for (int c = c0 + 1; c < c1; ++c) {
+    const int kc = child_rows_k(a, c, rho);
+    const double *Rc = a.Rin + (size_t)c * b * b;
+    double *slot = a.slots + (size_t)c * (b * b + a.nchunk * b);
+    for (int ch = 0, ra = 0; ra < kc; ++ch, ra += a.MT) {
+      const int M = min(a.MT, kc - ra);
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int r = idx / b, col = idx - r * b;
+        tile[r * a.lda + col] = Rc[(size_t)(ra + r) * b + col];
+      }
+      __syncthreads();
+      const int kk = hh_factor(Rr, b, k, tile, a.lda, M, b, taus, s);
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int r = idx / b, col = idx - r * b;
+        slot[(size_t)(ra + r) * b + col] = tile[r * a.lda + col];
+      }
+      for (int j = t; j < b; j += NT) slot[(size_t)b * b + ch * b + j] = j < kk ? taus[j] : 0.0;
+      hh_take_rows(Rr, b, k, kk, tile, a.lda, b);
+      k = kk;
+    }
+  }
+  double *Ro = a.Rout + (size_t)q * b * b;
+  for (int idx = t; idx < b * b; idx += NT) Ro[idx] = (idx / b) < k ? Rr[idx] : 0.0;
+}
+
+__global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *C = sm<double>(smem, a.oA), *V = sm<double>(smem, a.oB);
+  Scratch<double> s{sm<double>(smem, a.oRed), sm<double>(smem, a.oW), sm<double>(smem, a.oSc)};
+  double *taus = sm<double>(smem, a.oTau);
+  // CT lives right after V (MT x ncol)
+  const int q = blockIdx.x, t = threadIdx.x, b = a.b;
+  const int rho = dyn(a.rho_dyn, a.rho);
+  const int nc = dyn(a.ncol_dyn, a.ncol);
+  double *CT = V + (size_t)a.MT * a.lda;
+  const int c0 = q * a.G, c1 = min(a.nchild, c0 + a.G);
+  // replay the k sequence of the factorization
+  int kseq[64 + 1];  // k before each (child, chunk) step; G * nchunk <= 64 enforced by the host
+  int nsteps = 0;
+  int k = child_rows_k(a, c0, rho);
+  for (int c = c0 + 1; c < c1; ++c) {
+    const int kc = child_rows_k(a, c, rho);
+    for (int ra = 0; ra < kc; ra += a.MT) {
+      kseq[nsteps++] = k;
+      k = min(k + min(a.MT, kc - ra), b);
+    }
+  }
+  // load node C (k rows)
+  const double *Cn = a.Cin + (size_t)q * b * a.ldc;
+  for (int idx = t; idx < b * nc; idx += NT) {
+    const int r = idx / nc, col = idx - r * nc;
+    C[r * nc + col] = r < k ? Cn[(size_t)r * a.ldc + col] : 0.0;
+  }
+  __syncthreads();
+  int step = nsteps;
+  for (int c = c1 - 1; c > c0; --c) {
+    const int kc = child_rows_k(a, c, rho);
+    const double *slot = a.slots + (size_t)c * (b * b + a.nchunk * b);
+    double *Cc = a.Cout + (size_t)c * b * a.ldc;
+    const int nch = (kc + a.MT - 1) / a.MT;
+    for (int ch = nch - 1; ch >= 0; --ch) {
+      const int ra = ch * a.MT, M = min(a.MT, kc - ra);
+      const int kb = kseq[--step], ka = min(kb + M, b);
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int r = idx / b, col = idx - r * b;
+        V[r * a.lda + col] = slot[(size_t)(ra + r) * b + col];
+      }
+      for (int j = t; j < b; j += NT) taus[j] = slot[(size_t)b * b + ch * b + j];
+      for (int idx = t; idx < M * nc; idx += NT) {
+        const int r = idx / nc, col = idx - r * nc;
+        CT[r * nc + col] = (kb + r < ka) ? C[(kb + r) * nc + col] : 0.0;
+      }
+      __syncthreads();
+      hh_apply(V, a.lda, taus, kb, M, b, C, nc, CT, nc, nc, s);
+      __syncthreads();
+      for (int idx = t; idx < M * nc; idx += NT) {
+        const int r = idx / nc, col = idx - r * nc;
+        Cc[(size_t)(ra + r) * a.ldc + col] = CT[r * nc + col];
+      }
+      __syncthreads();
+    }
+  }
+  // first child keeps the remaining rows
+  const int k0 = child_rows_k(a, c0, rho);
+  double *Cc = a.Cout + (size_t)c0 * b * a.ldc;
+  for (int idx = t; idx < k0 * nc; idx += NT) {
+    const int r = idx / nc, col = idx - r * nc;
+    Cc[(size_t)r * a.ldc + col] = C[r * nc + col];
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// sweep 2 leaf: (A) apply Q_n to C_p, form Y_n slabs, factor V(Y_n) slabs
+//               (B) core 0: push and factor V(X_0 x_3 P)
+//               (last) apply Q_{N-1} and write the last output core
+// ------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *Q = sm<T>(smem, a.oQ), *CT = sm<T>(smem, a.oCT), *CR = sm<T>(smem, a.oCR), *Rr = sm<T>(smem, a.oRr);
+  T *Xs = sm<T>(smem, a.oXs), *Ps = sm<T>(smem, a.oPs);
+  Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
+  T *tq = sm<T>(smem, a.oTq), *tv = sm<T>(smem, a.oTv);
+  const int p = blockIdx.x, t = threadIdx.x;
+  const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
+  const int K1 = a.K1;
+  const int L = a.mode == 1 ? 1 : *a.Lcur;  // rows per slice of V(Y_n)
+  const int b1 = a.b1;
+  // number of sweep-1 reflector rows owned by this leaf, and its C rows
+  int kq = 0;
+  if (a.mode != 1) {
+    kq = (int)min64((s1 - s0) * (int64_t)K1, b1);
+    const double *Cp = a.Cleaf + (size_t)p * b1 * a.ldc;
+    for (int idx = t; idx < b1 * L; idx += NT) {
+      const int r = idx / L, c = idx - r * L;
+      CR[idx] = r < kq ? (T)Cp[(size_t)r * a.ldc + c] : T(0);
+    }
+  } else {
+    for (int idx = t; idx < K1 * a.cin; idx += NT) Ps[idx] = (T)a.Pm[idx];
+  }
+  for (int idx = t; idx < K1 * K1; idx += NT) Rr[idx] = T(0);
+  __syncthreads();
+  int kv = 0;  // rows of the running V-QR factor
+  // tiles in reverse slice order
+  const int64_t ntiles = (s1 - s0 + a.g.Tt - 1) / a.g.Tt;
+  for (int64_t ti = ntiles - 1; ti >= 0; --ti) {
+    const int64_t i0 = s0 + ti * a.g.Tt;
+    const int nt = (int)min((int64_t)a.g.Tt, s1 - i0);
+    int Mv = nt * L;  // rows of this V tile
+    if (a.mode != 1) {
+      // (1) apply this tile's sweep-1 reflectors to [CR; CT]
+      const int M1 = nt * K1;
+      const int kb = (int)min64((i0 - s0) * (int64_t)K1, b1);
+      const int ka = min(kb + M1, b1);
+      const T *src = a.qrefl + (size_t)i0 * K1 * b1;
+      for (int idx = t; idx < M1 * b1; idx += NT) {
+        const int r = idx / b1, c = idx - r * b1;
+        Q[r * a.ldq + c] = src[idx];
+      }
+      for (int j = t; j < ka; j += NT) tq[j] = a.qtau[(size_t)i0 * b1 + j];
+      for (int idx = t; idx < M1 * L; idx += NT) {
+        const int r = idx / L, c = idx - r * L;
+        CT[idx] = (kb + r < ka) ? CR[(kb + r) * L + c] : T(0);
+      }
+      __syncthreads();
+      hh_apply(Q, a.ldq, tq, kb, M1, b1, CR, L, CT, L, L, s);
+      __syncthreads();
+      if (a.mode == 2) {
+        // last core: Y[l, i, 0] = CT[(i - i0)][l]  (K1 == 1)
+        for (int idx = t; idx < nt * L; idx += NT) {
+          const int il = idx / L, l = idx - il * L;
+          a.out[(size_t)l + (size_t)L * (i0 + il)] = CT[il * L + l];
+        }
+        __syncthreads();
+        continue;
+      }
+      // (2) V tile: row (i - i0) * L + l, column k  <-  CT[(i - i0) * K1 + k][l]   (reuse Q)
+      for (int idx = t; idx < Mv * K1; idx += NT) {
+        const int r = idx / K1, kc = idx - r * K1;
+        const int il = r / L, l = r - il * L;
+        Q[r * a.ldv + kc] = CT[(il * K1 + kc) * L + l];
+      }
+      __syncthreads();
+    } else {
+      // core 0: V tile row (i - i0), column k = sum_c X0[i + I c] P[k][c]
+      for (int idx = t; idx < Mv * K1; idx += NT) Q[(idx / K1) * a.ldv + (idx % K1)] = T(0);
+      for (int c0 = 0; c0 < a.cin; c0 += a.CC) {
+        const int cc_n = min(a.CC, a.cin - c0);
+        __syncthreads();
+        for (int idx = t; idx < cc_n * nt; idx += NT) {
+          const int cc = idx / nt, il = idx - cc * nt;
+          Xs[idx] = a.X0[(size_t)(i0 + il) + (size_t)a.g.I * (c0 + cc)];
+        }
+        __syncthreads();
+        for (int idx = t; idx < Mv * K1; idx += NT) {
+          const int il = idx / K1, kc = idx - il * K1;
+          T acc = Q[il * a.ldv + kc];
+          for (int c = max(kc, c0); c < c0 + cc_n; ++c) acc += Ps[kc * a.cin + c] * Xs[(c - c0) * nt + il];
+          Q[il * a.ldv + kc] = acc;
+        }
+      }
+      __syncthreads();
+    }
+    // (3) factor the V tile under the running factor
+    const int kk = hh_factor(Rr, K1, kv, Q, a.ldv, Mv, K1, tv, s);
+    T *dst = a.vrefl + (size_t)i0 * L * K1;
+    for (int idx = t; idx < Mv * K1; idx += NT) {
+      const int r = idx / K1, c = idx - r * K1;
+      dst[idx] = Q[r * a.ldv + c];
+    }
+    for (int j = t; j < kk; j += NT) a.vtau[(size_t)i0 * K1 + j] = tv[j];
+    hh_take_rows(Rr, K1, kv, kk, Q, a.ldv, K1);
+    kv = kk;
+  }
+  if (a.mode == 2) return;
+  double *Ro = a.Rleaf + (size_t)p * K1 * K1;
+  for (int idx = t; idx < K1 * K1; idx += NT) Ro[idx] = (idx / K1) < kv ? (double)Rr[idx] : 0.0;
+}
+
+// ------------------------------------------------------------------------------------
+// sweep 2 output: core n = Q'_n [U_p; 0]
+// ------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_s2_out(OutArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *V = sm<T>(smem, a.oV), *CT = sm<T>(smem, a.oCT), *CR = sm<T>(smem, a.oCR);
+  Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
+  T *tv = sm<T>(smem, a.oTau);
+  const int p = blockIdx.x, t = threadIdx.x;
+  const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
+  const int K1 = a.K1, L = *a.Lcur, Ln = *a.Lnext;
+  const int kleaf = (int)min64((s1 - s0) * (int64_t)L, K1);
+  const double *Up = a.Uleaf + (size_t)p * K1 * a.ldc;
+  for (int idx = t; idx < K1 * Ln; idx += NT) {
+    const int r = idx / Ln, c = idx - r * Ln;
+    CR[idx] = r < kleaf ? (T)Up[(size_t)r * a.ldc + c] : T(0);
+  }
+  __syncthreads();
+  // the V-QR processed tiles in reverse slice order, so Q' is applied in forward order
+  for (int64_t i0 = s0; i0 < s1; i0 += a.g.Tt) {
+    const int nt = (int)min((int64_t)a.g.Tt, s1 - i0);
+    const int Mv = nt * L;
+    const int ka = (int)min64((s1 - i0) * (int64_t)L, K1);
+    const int kb = (int)min64((s1 - i0 - nt) * (int64_t)L, K1);
+    const T *src = a.vrefl + (size_t)i0 * L * K1;
+    for (int idx = t; idx < Mv * K1; idx += NT) {
+      const int r = idx / K1, c = idx - r * K1;
+      V[r * a.ldv + c] = src[idx];
+    }
+    for (int j = t; j < ka; j += NT) tv[j] = a.vtau[(size_t)i0 * K1 + j];
+    for (int idx = t; idx < Mv * Ln; idx += NT) {
+      const int r = idx / Ln, c = idx - r * Ln;
+      CT[idx] = (kb + r < ka) ? CR[(kb + r) * Ln + c] : T(0);
+    }
+    __syncthreads();
+    hh_apply(V, a.ldv, tv, kb, Mv, K1, CR, Ln, CT, Ln, Ln, s);
+    __syncthreads();
+    // rows (i - i0) * L + l, column l'  ->  out[l + L (i + I l')]
+    for (int idx = t; idx < Mv * Ln; idx += NT) {
+      const int c = idx / Mv, r = idx - c * Mv;
+      a.out[(size_t)L * i0 + r + (size_t)L * a.g.I * c] = CT[r * Ln + c];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// FP64 one-sided Jacobi SVD of the root factor + rank choice (one CTA)
+// ------------------------------------------------------------------------------------
+
+constexpr int SVD_NT = 512;
+
+__global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = a.K, t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
+  const int Lc = *a.Lcur;
+  const int kroot = (int)min64((int64_t)Lc * a.In, K);
+  const bool wide = kroot < K;
+  const int ms = K, ns = wide ? kroot : K;  // A is ms x ns, column-major
+  double *A = reinterpret_cast<double *>(smem);
+  double *Vm = A + (size_t)ms * ns;
+  double *sig = Vm + (size_t)ns * ns;
+  int *pos = reinterpret_cast<int *>(sig + ns);  // 2 * (ns + 1)
+  int *ord = pos + 2 * (ns + 2);
+  int *flag = ord + ns + 1;
+  for (int idx = t; idx < ms * ns; idx += SVD_NT) {
+    const int c = idx / ms, r = idx - c * ms;
+    A[idx] = wide ? a.Rroot[(size_t)c * K + r] : a.Rroot[(size_t)r * K + c];
+  }
+  for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (idx / ns) == (idx % ns) ? 1.0 : 0.0;
+  const int n2 = (ns + 1) & ~1;
+  for (int i = t; i < n2; i += SVD_NT) pos[i] = i;
+  if (t == 0) flag[0] = 0;
+  __syncthreads();
+  const double tol = 1e-15 * (double)ms;
+  int sweeps = 0, converged = 0;
+  int cur = 0;
+  for (sweeps = 1; sweeps <= 60 && ns > 1; ++sweeps) {
+    if (t == 0) flag[0] = 0;
+    __syncthreads();
+    for (int round = 0; round < n2 - 1; ++round) {
+      int *P = pos + cur * (ns + 2);
+      for (int pr = warp; pr < n2 / 2; pr += nwarp) {
+        int pp = P[pr], qq = P[n2 - 1 - pr];
+        if (pp >= ns || qq >= ns) continue;
+        if (pp > qq) {
+          const int tmp = pp;
+          pp = qq;
+          qq = tmp;
+        }
+        double *bp = A + (size_t)pp * ms, *bq = A + (size_t)qq * ms;
+        double al = 0, be = 0, ga = 0;
+        for (int r = lane; r < ms; r += 32) {
+          const double x = bp[r], y = bq[r];
+          al += x * x;
+          be += y * y;
+          ga += x * y;
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
+        const double zeta = (be - al) / (2.0 * ga);
+        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        for (int r = lane; r < ms; r += 32) {
+          const double x = bp[r], y = bq[r];
+          bp[r] = cs * x - sn * y;
+          bq[r] = sn * x + cs * y;
+        }
+        double *vp = Vm + (size_t)pp * ns, *vq = Vm + (size_t)qq * ns;
+        for (int r = lane; r < ns; r += 32) {
+          const double x = vp[r], y = vq[r];
+          vp[r] = cs * x - sn * y;
+          vq[r] = sn * x + cs * y;
+        }
+        if (lane == 0) flag[0] = 1;
+      }
+      __syncthreads();
+      // tournament rotation: keep position 0, rotate the rest by one
+      int *Pn = pos + (cur ^ 1) * (ns + 2);
+      for (int i = t; i < n2; i += SVD_NT) Pn[i] = i == 0 ? P[0] : (i == 1 ? P[n2 - 1] : P[i - 1]);
+      cur ^= 1;
+      __syncthreads();
+    }
+    const int any = flag[0];
+    __syncthreads();
+    if (!any) {
+      converged = 1;
+      break;
+    }
+  }
+  if (ns <= 1) converged = 1;
+  // singular values
+  for (int c = warp; c < ns; c += nwarp) {
+    double ss = 0;
+    for (int r = lane; r < ms; r += 32) ss += A[(size_t)c * ms + r] * A[(size_t)c * ms + r];
+    ss = warp_sum(ss);
+    if (lane == 0) sig[c] = sqrt(ss);
+  }
+  __syncthreads();
+  if (t == 0) {
+    // stable insertion sort by decreasing sigma
+    for (int i = 0; i < ns; ++i) ord[i] = i;
+    for (int i = 1; i < ns; ++i) {
+      const int key = ord[i];
+      int j = i - 1;
+      while (j >= 0 && sig[ord[j]] < sig[key]) {
+        ord[j + 1] = ord[j];
+        --j;
+      }
+      ord[j + 1] = key;
+    }
+    bool finite = true;
+    for (int i = 0; i < ns; ++i) finite = finite && isfinite(sig[i]);
+    if (a.n == 0) {
+      double s2 = 0.0;
+      for (int i = ns - 1; i >= 0; --i) s2 += sig[ord[i]] * sig[ord[i]];
+      const double nrm = sqrt(s2);
+      a.scal[0] = nrm;
+      a.scal[1] = a.N > 1 ? a.eps * nrm / sqrt((double)(a.N - 1)) : 0.0;
+    }
+    const double d2 = a.scal[1] * a.scal[1];
+    // L = min{ L >= 1 : tail(L) <= delta^2 }, tail(l) = sum_{j >= l} sigma_j^2 accumulated
+    // from the smallest value upward; tail(ns) = 0 always qualifies
+    int L = ns;
+    double tl = 0.0;
+    for (int l = ns - 1; l >= 1; --l) {
+      tl += sig[ord[l]] * sig[ord[l]];
+      if (tl <= d2)
+        L = l;
+      else
+        break;
+    }
+    *a.Lnext = L;
+    if (!finite || !converged) *a.status = TT_ERR_NUMERICAL;
+    flag[1] = L;
+  }
+  __syncthreads();
+  const int L = flag[1];
+  // outputs
+  for (int idx = t; idx < K * L; idx += SVD_NT) {
+    const int r = idx / L, l = idx - r * L;
+    const int c = ord[l];
+    const double sg = sig[c];
+    if (!wide) {
+      // R' = U S V^T : U_hat = A(:, c) / sigma, C_next = V(:, c) sigma
+      a.Uhat[(size_t)r * a.ldu + l] = sg > 0.0 ? A[(size_t)c * ms + r] / sg : (r == l ? 1.0 : 0.0);
+      a.Cnext[(size_t)r * a.ldu + l] = Vm[(size_t)c * ns + r] * sg;
+    } else {
+      // R'^T = U' S V'^T : U_hat = V'(:, c) (kroot rows), C_next = A(:, c) (= U' sigma)
+      if (r < kroot) a.Uhat[(size_t)r * a.ldu + l] = Vm[(size_t)c * ns + r];
+      a.Cnext[(size_t)r * a.ldu + l] = A[(size_t)c * ms + r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// norm of the pushed first core: sum_{i,k} (sum_c X0[i + I c] P[k][c])^2
+// ------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_push_sumsq(const T *X0, int64_t I, int cin, int K, const double *Pm,
+                                                   double *partial) {
+  __shared__ double red[NT / 32];
+  double acc = 0.0;
+  const int64_t total = I * K;
+  for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < total; e += (int64_t)gridDim.x * NT) {
+    const int64_t i = e / K;
+    const int kk = (int)(e - i * K);
+    double v = 0.0;
+    if (Pm) {
+      for (int c = kk; c < cin; ++c) v += (double)X0[i + I * c] * Pm[kk * cin + c];
+    } else {
+      v = (double)X0[i];
+    }
+    acc += v * v;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_init_ctl(int *L, int N, int *status) {
+  for (int i = threadIdx.x; i <= N; i += blockDim.x) L[i] = 1;
+  if (threadIdx.x < 4) status[threadIdx.x] = 0;
+}
+
+__global__ void k_sum_sqrt(const double *partial, int n, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += partial[i];
+    out[0] = sqrt(s);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kG = 8;          // tree fan-in
+constexpr int kMaxLev = 10;
+constexpr size_t kSmemBudget = 220 * 1024;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes, size_t al = 16) {
+    off = align_up(off, al);
+    const size_t o = off;
+    off += bytes;
+    return o;
+  }
+};
+
+struct Tree {
+  int nlev = 0;               // number of factor levels (0 if a single leaf)
+  int count[kMaxLev + 1];     // count[0] = leaves, count[nlev] = 1
+  int lpc[kMaxLev + 1];       // leaves per node at each level
+  size_t slot_off[kMaxLev];   // slot index offset of the children of level l+1 (children at level l)
+  size_t nslots = 0;
+  size_t node_off[kMaxLev + 1];  // offset (in nodes) of level l in per-level buffers
+  size_t nnodes = 0;
+};
+
+Tree make_tree(int P) {
+  Tree tr;
+  tr.count[0] = P;
+  tr.lpc[0] = 1;
+  int l = 0;
+  while (tr.count[l] > 1) {
+    tr.count[l + 1] = (tr.count[l] + kG - 1) / kG;
+    tr.lpc[l + 1] = tr.lpc[l] * kG;
+    ++l;
+  }
+  tr.nlev = l;
+  size_t so = 0, no = 0;
+  for (int i = 0; i <= tr.nlev; ++i) {
+    tr.node_off[i] = no;
+    no += tr.count[i];
+    if (i < tr.nlev) {
+      tr.slot_off[i] = so;
+      so += tr.count[i];
+    }
+  }
+  tr.nslots = so;
+  tr.nnodes = no;
+  return tr;
+}
+
+int leaves_for(int64_t I, int nsm) {
+  const int64_t target = 2 * (int64_t)nsm;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(I, target));
+}
+
+template <typename T>
+struct SmemS1 {
+  int oRr, oTile, oXs, oPs, oRed, oW, oSc, oTau, ldt;
+  size_t bytes;
+};
+
+template <typename T>
+SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC) {
+  SmemS1<T> m;
+  Carve c;
+  m.ldt = b + 1;
+  m.oRr = (int)c.take(sizeof(T) * b * b);
+  m.oTile = (int)c.take(sizeof(T) * (size_t)Tt * rho * m.ldt);
+  m.oXs = (int)c.take(sizeof(T) * (size_t)CC * Tt * b);
+  m.oPs = (int)c.take(sizeof(T) * (size_t)rho * cin);
+  m.oRed = (int)c.take(sizeof(T) * NT);
+  m.oW = (int)c.take(sizeof(T) * std::max(b, 1));
+  m.oSc = (int)c.take(sizeof(T) * 2);
+  m.oTau = (int)c.take(sizeof(T) * b);
+  m.bytes = c.off;
+  return m;
+}
+
+template <typename T>
+struct SmemS2 {
+  int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv, ldq, ldv;
+  size_t bytes;
+};
+
+// mode A/last: b1 = R_n, K1 = K_{n+1}, Lmax = max rows per slice of V(Y_n) (<= K_n)
+template <typename T>
+SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC) {
+  SmemS2<T> m;
+  Carve c;
+  m.ldq = b1 + 1;
+  m.ldv = K1 + 1;
+  size_t qrows = mode == 1 ? 0 : (size_t)Tt * K1;
+  size_t vrows = (size_t)Tt * (mode == 1 ? 1 : Lmax);
+  size_t qbytes = std::max(qrows * m.ldq, mode == 2 ? 0 : vrows * m.ldv) * sizeof(T);
+  m.oQ = (int)c.take(qbytes);
+  m.oCT = (int)c.take(sizeof(T) * (mode == 1 ? 1 : qrows * Lmax));
+  m.oCR = (int)c.take(sizeof(T) * (mode == 1 ? 1 : (size_t)b1 * Lmax));
+  m.oRr = (int)c.take(sizeof(T) * (size_t)K1 * K1);
+  m.oXs = (int)c.take(sizeof(T) * (mode == 1 ? (size_t)CC * Tt : 1));
+  m.oPs = (int)c.take(sizeof(T) * (mode == 1 ? (size_t)K1 * cin : 1));
+  m.oRed = (int)c.take(sizeof(T) * NT);
+  m.oW = (int)c.take(sizeof(T) * std::max(std::max(b1, K1), Lmax));
+  m.oSc = (int)c.take(sizeof(T) * 2);
+  m.oTq = (int)c.take(sizeof(T) * std::max(b1, 1));
+  m.oTv = (int)c.take(sizeof(T) * K1);
+  m.bytes = c.off;
+  return m;
+}
+
+template <typename T>
+struct SmemOut {
+  int oV, oCT, oCR, oRed, oW, oSc, oTau, ldv;
+  size_t bytes;
+};
+
+template <typename T>
+SmemOut<T> smem_out(int K1, int Lmax, int Tt) {
+  SmemOut<T> m;
+  Carve c;
+  m.ldv = K1 + 1;
+  m.oV = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * m.ldv);
+  m.oCT = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * K1);
+  m.oCR = (int)c.take(sizeof(T) * (size_t)K1 * K1);
+  m.oRed = (int)c.take(sizeof(T) * NT);
+  m.oW = (int)c.take(sizeof(T) * std::max(K1, 1));
+  m.oSc = (int)c.take(sizeof(T) * 2);
+  m.oTau = (int)c.take(sizeof(T) * K1);
+  m.bytes = c.off;
+  return m;
+}
+
+struct SmemTree {
+  int oA, oB, oRed, oW, oSc, oTau, lda, MT, nchunk;
+  size_t bytes;
+};
+
+// factor: A = Rr (b x b), B = tile (MT x lda); apply: A = C (b x cmax), B = V (MT x lda) + CT (MT x cmax)
+SmemTree smem_tree(int b, int cmax) {
+  SmemTree m;
+  m.lda = b + 1;
+  for (m.MT = b; m.MT > 1; m.MT = (m.MT + 1) / 2) {
+    Carve c;
+    size_t A = std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double);
+    size_t B = ((size_t)m.MT * m.lda + (size_t)m.MT * cmax) * sizeof(double);
+    c.take(A);
+    c.take(B);
+    c.take(sizeof(double) * NT);
+    c.take(sizeof(double) * std::max(b, cmax));
+    c.take(sizeof(double) * 2);
+    c.take(sizeof(double) * b);
+    if (c.off <= kSmemBudget) break;
+  }
+  Carve c;
+  m.oA = (int)c.take(std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double));
+  m.oB = (int)c.take(((size_t)m.MT * m.lda + (size_t)m.MT * cmax) * sizeof(double));
+  m.oRed = (int)c.take(sizeof(double) * NT);
+  m.oW = (int)c.take(sizeof(double) * std::max(b, cmax));
+  m.oSc = (int)c.take(sizeof(double) * 2);
+  m.oTau = (int)c.take(sizeof(double) * b);
+  m.bytes = c.off;
+  m.nchunk = (b + m.MT - 1) / m.MT;
+  return m;
+}
+
+size_t smem_svd(int K) {
+  return sizeof(double) * ((size_t)K * K * 2 + K) + sizeof(int) * (3 * (size_t)K + 16);
+}
+
+struct CorePlan {
+  int64_t I = 0;
+  int R0 = 1, R1 = 1;  // input ranks
+  int K0 = 1, K1 = 1;  // ranks after sweep 1
+  int P = 1, Tt = 1;
+  Tree tree;
+  size_t refl_off = 0, tau_off = 0, slot_off = 0;  // sweep-1 storage (n >= 1)
+};
+
+}  // namespace
+
+struct RoundPlan {
+  int N = 0;
+  int dtype = TT_F64;
+  int nsm = 152;
+  int bmax = 1;  // max input rank
+  std::vector<CorePlan> core;
+  // workspace layout (bytes)
+  size_t off_ctl = 0, off_L = 0, off_scal = 0, off_status = 0, off_P = 0;
+  size_t off_R = 0, off_C1 = 0, off_C2 = 0, off_slots2 = 0, off_refl2 = 0, off_tau2 = 0, off_part = 0;
+  size_t max_nodes = 0, max_slots = 0;
+  size_t total = 0;
+  int tree_MT[TT_MAX_RANK + 1];
+};
+
+static int device_sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+  return n;
+}
+
+template <typename T>
+static bool choose_tiles(RoundPlan &pl) {
+  const int N = pl.N;
+  for (int n = 0; n < N; ++n) {
+    CorePlan &c = pl.core[n];
+    const int64_t per_leaf = (c.I + c.P - 1) / c.P;
+    int best = 0;
+    const int CC = 8;
+    const int maxT = n == 0 ? 512 : 64;
+    for (int Tt = 1; Tt <= maxT && Tt <= per_leaf; ++Tt) {
+      bool ok = true;
+      if (n >= 1) {
+        const int rows = Tt * c.K1;
+        if (rows > 512 && Tt > 1) break;
+        ok = ok && smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC).bytes <= kSmemBudget;
+        if (n < N - 1) {
+          ok = ok && smem_s2<T>(0, c.R0, c.K1, c.K0, Tt, 1, CC).bytes <= kSmemBudget;
+          ok = ok && smem_out<T>(c.K1, c.K0, Tt).bytes <= kSmemBudget;
+        } else {
+          ok = ok && smem_s2<T>(2, c.R0, c.K1, c.K0, Tt, 1, CC).bytes <= kSmemBudget;
+        }
+      } else {
+        ok = ok && smem_s2<T>(1, 1, c.K1, 1, Tt, c.R1, CC).bytes <= kSmemBudget;
+        ok = ok && smem_out<T>(c.K1, 1, Tt).bytes <= kSmemBudget;
+      }
+      if (!ok) break;
+      best = Tt;
+    }
+    if (best == 0) return false;
+    c.Tt = best;
+  }
+  return true;
+}
+
+template <typename T>
+static int make_plan(const tt_tensor *x, RoundPlan &pl) {
+  const int N = x->N;
+  pl.N = N;
+  pl.dtype = x->dtype;
+  pl.nsm = device_sm_count();
+  pl.core.assign(N, CorePlan());
+  pl.bmax = 1;
+  for (int n = 0; n < N; ++n) {
+    CorePlan &c = pl.core[n];
+    c.I = x->I[n];
+    c.R0 = (int)x->R[n];
+    c.R1 = (int)x->R[n + 1];
+    pl.bmax = std::max(pl.bmax, std::max(c.R0, c.R1));
+  }
+  // ranks after the right-to-left sweep: K_n = min(R_n, I_n K_{n+1})
+  pl.core[N - 1].K1 = 1;
+  for (int n = N - 1; n >= 1; --n) {
+    CorePlan &c = pl.core[n];
+    c.K0 = (int)std::min<int64_t>(c.R0, c.I * c.K1);
+    pl.core[n - 1].K1 = c.K0;
+  }
+  pl.core[0].K0 = 1;
+  for (int n = 0; n < N; ++n) {
+    CorePlan &c = pl.core[n];
+    c.P = leaves_for(c.I, pl.nsm);
+    c.tree = make_tree(c.P);
+  }
+  if (N > 1 && !choose_tiles<T>(pl)) return TT_ERR_UNSUPPORTED;
+  // svd and tree shared-memory limits
+  for (int n = 0; n + 1 < N; ++n)
+    if (smem_svd(pl.core[n].K1) > kSmemBudget) return TT_ERR_UNSUPPORTED;
+  // workspace layout
+  Carve w;
+  pl.off_L = w.take(sizeof(int) * (N + 1), 256);
+  pl.off_scal = w.take(sizeof(double) * 4, 256);
+  pl.off_status = w.take(sizeof(int) * 4, 256);
+  pl.off_P = w.take(sizeof(double) * (size_t)pl.bmax * pl.bmax, 256);
+  size_t max_nodes = 1, max_slots = 1, max_refl2 = 1, max_tau2 = 1;
+  const size_t B = (size_t)pl.bmax;
+  for (int n = 0; n < N; ++n) {
+    CorePlan &c = pl.core[n];
+    max_nodes = std::max(max_nodes, c.tree.nnodes);
+    max_slots = std::max(max_slots, c.tree.nslots);
+    if (n >= 1) {
+      c.refl_off = w.take(sizeof(T) * (size_t)c.I * c.K1 * c.R0, 256);
+      c.tau_off = w.take(sizeof(T) * (size_t)c.I * c.R0, 256);
+      const SmemTree st = smem_tree(c.R0, 1);
+      c.slot_off = w.take(sizeof(double) * c.tree.nslots * ((size_t)c.R0 * c.R0 + (size_t)st.nchunk * c.R0), 256);
+    }
+    if (n < N - 1) {
+      max_refl2 = std::max(max_refl2, (size_t)c.I * c.K0 * c.K1);
+      max_tau2 = std::max(max_tau2, (size_t)c.I * c.K1);
+    }
+  }
+  pl.max_nodes = max_nodes;
+  pl.max_slots = max_slots;
+  pl.off_R = w.take(sizeof(double) * max_nodes * B * B, 256);
+  pl.off_C1 = w.take(sizeof(double) * max_nodes * B * B, 256);
+  pl.off_C2 = w.take(sizeof(double) * max_nodes * B * B, 256);
+  pl.off_slots2 = w.take(sizeof(double) * max_slots * (B * B + B * B), 256);
+  pl.off_refl2 = w.take(sizeof(T) * max_refl2, 256);
+  pl.off_tau2 = w.take(sizeof(T) * max_tau2, 256);
+  pl.off_part = w.take(sizeof(double) * 4096, 256);
+  pl.total = w.off;
+  return TT_OK;
+}
+
+int round_workspace(const tt_tensor *x, size_t *bytes) {
+  RoundPlan pl;
+  int st = x->dtype == TT_F64 ? make_plan<double>(x, pl) : make_plan<float>(x, pl);
+  if (st) return st;
+  *bytes = pl.total;
+  return TT_OK;
+}
+
+#define TT_CUDA(call)                          \
+  do {                                         \
+    cudaError_t e_ = (call);                   \
+    if (e_ != cudaSuccess) return TT_ERR_CUDA; \
+  } while (0)
+
+template <typename K>
+static int set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) TT_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return TT_OK;
+}
+
+// level-by-level tree factorization of the leaf R's in Rbuf level 0; root ends at level nlev
+static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, double *Rbase, double *slots,
+                       int B, cudaStream_t st) {
+  const SmemTree sm = smem_tree(b, 1);
+  int r = set_smem(k_tree_factor, sm.bytes);
+  if (r) return r;
+  for (int l = 0; l < tr.nlev; ++l) {
+    TreeArgs a{};
+    a.Rin = Rbase + tr.node_off[l] * B * B;
+    a.Rout = Rbase + tr.node_off[l + 1] * B * B;
+    a.slots = slots + tr.slot_off[l] * ((size_t)b * b + (size_t)sm.nchunk * b);
+    a.nchild = tr.count[l];
+    a.G = kG;
+    a.b = b;
+    a.MT = sm.MT;
+    a.nchunk = sm.nchunk;
+    a.I = I;
+    a.P = tr.count[0];
+    a.lpc = tr.lpc[l];
+    a.rho = rho;
+    a.rho_dyn = rho_dyn;
+    a.lda = sm.lda;
+    a.oA = sm.oA;
+    a.oB = sm.oB;
+    a.oRed = sm.oRed;
+    a.oW = sm.oW;
+    a.oSc = sm.oSc;
+    a.oTau = sm.oTau;
+    k_tree_factor<<<tr.count[l + 1], NT, sm.bytes, st>>>(a);
+    TT_CUDA(cudaGetLastError());
+  }
+  return TT_OK;
+}
+
+// root-to-leaves application; the root C sits at Cbase level nlev; leaf C's end at level 0
+static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, int ncol, const int *ncol_dyn,
+                      int cmax, double *Cbase, const double *slots, int B, cudaStream_t st) {
+  const SmemTree sm = smem_tree(b, cmax);
+  const SmemTree smf = smem_tree(b, 1);  // the slots hold the factorization's chunking
+  SmemTree use = sm;
+  use.MT = smf.MT;
+  use.nchunk = smf.nchunk;
+  {
+    Carve c;
+    use.oA = (int)c.take(std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double));
+    use.oB = (int)c.take(((size_t)use.MT * use.lda + (size_t)use.MT * cmax) * sizeof(double));
+    use.oRed = (int)c.take(sizeof(double) * NT);
+    use.oW = (int)c.take(sizeof(double) * std::max(b, cmax));
+    use.oSc = (int)c.take(sizeof(double) * 2);
+    use.oTau = (int)c.take(sizeof(double) * b);
+    use.bytes = c.off;
+  }
+  if (use.bytes > kSmemBudget || kG * use.nchunk > 64) return TT_ERR_UNSUPPORTED;
+  int r = set_smem(k_tree_apply, use.bytes);
+  if (r) return r;
+  for (int l = tr.nlev - 1; l >= 0; --l) {
+    TreeArgs a{};
+    a.Cin = Cbase + tr.node_off[l + 1] * B * B;
+    a.Cout = Cbase + tr.node_off[l] * B * B;
+    a.slots = const_cast<double *>(slots) + tr.slot_off[l] * ((size_t)b * b + (size_t)use.nchunk * b);
+    a.nchild = tr.count[l];
+    a.G = kG;
+    a.b = b;
+    a.MT = use.MT;
+    a.nchunk = use.nchunk;
+    a.I = I;
+    a.P = tr.count[0];
+    a.lpc = tr.lpc[l];
+    a.rho = rho;
+    a.rho_dyn = rho_dyn;
+    a.ncol = ncol;
+    a.ncol_dyn = ncol_dyn;
+    a.ldc = B;
+    a.lda = use.lda;
+    a.oA = use.oA;
+    a.oB = use.oB;
+    a.oRed = use.oRed;
+    a.oW = use.oW;
+    a.oSc = use.oSc;
+    a.oTau = use.oTau;
+    k_tree_apply<<<tr.count[l], NT, use.bytes, st>>>(a);
+    TT_CUDA(cudaGetLastError());
+  }
+  return TT_OK;
+}
+
+template <typename T>
+static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st) {
+  const int N = pl.N;
+  const int B = pl.bmax;
+  double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
+  const double *Pm = nullptr;  // root R of the previous core (device), K_{n+1} x R_{n+1}
+  for (int n = N - 1; n >= 1; --n) {
+    const CorePlan &c = pl.core[n];
+    const SmemS1<T> m = smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8);
+    S1Args<T> a{};
+    a.X = reinterpret_cast<const T *>(x->cores[n]);
+    a.g = Geom{c.I, c.P, c.Tt};
+    a.b = c.R0;
+    a.cin = c.R1;
+    a.rho = c.K1;
+    a.Pm = Pm;
+    a.refl = reinterpret_cast<T *>(ws + c.refl_off);
+    a.tau = reinterpret_cast<T *>(ws + c.tau_off);
+    a.Rleaf = Rbase + c.tree.node_off[0] * B * B;
+    a.CC = 8;
+    a.oRr = m.oRr;
+    a.oTile = m.oTile;
+    a.oXs = m.oXs;
+    a.oPs = m.oPs;
+    a.oRed = m.oRed;
+    a.oW = m.oW;
+    a.oSc = m.oSc;
+    a.oTau = m.oTau;
+    a.ldt = m.ldt;
+    int r = set_smem(k_s1_leaf<T>, m.bytes);
+    if (r) return r;
+    k_s1_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+    TT_CUDA(cudaGetLastError());
+    r = tree_factor(c.tree, c.R0, c.I, c.K1, nullptr, Rbase, reinterpret_cast<double *>(ws + c.slot_off), B, st);
+    if (r) return r;
+    // move the root to the dedicated pushed-factor region so that the next core's leaves
+    // can overwrite the tree levels
+    double *root = Rbase + c.tree.node_off[c.tree.nlev] * B * B;
+    double *keep = reinterpret_cast<double *>(ws + pl.off_P);
+    // root is b x b row-major with K0 valid rows; the push needs K0 x R0 with ld R0 == b
+    TT_CUDA(cudaMemcpyAsync(keep, root, sizeof(double) * (size_t)c.R0 * c.R0, cudaMemcpyDeviceToDevice, st));
+    Pm = keep;
+  }
+  return TT_OK;
+}
+
+template <typename T>
+static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_tensor *out, unsigned char *ws,
+                     cudaStream_t st) {
+  const int N = pl.N;
+  const int B = pl.bmax;
+  int *dL = reinterpret_cast<int *>(ws + pl.off_L);
+  double *dscal = reinterpret_cast<double *>(ws + pl.off_scal);
+  int *dstatus = reinterpret_cast<int *>(ws + pl.off_status);
+  // L[0] = L[N] = 1 are fixed; the others are written by the SVD kernels
+  k_init_ctl<<<1, 32, 0, st>>>(dL, N, dstatus);
+  TT_CUDA(cudaGetLastError());
+  int r = sweep1<T>(pl, x, ws, st);
+  if (r) return r;
+  double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
+  double *C1 = reinterpret_cast<double *>(ws + pl.off_C1);
+  double *C2 = reinterpret_cast<double *>(ws + pl.off_C2);
+  const double *P1 = reinterpret_cast<const double *>(ws + pl.off_P);  // R_1 pushed into core 0
+  double *slots2 = reinterpret_cast<double *>(ws + pl.off_slots2);
+  T *refl2 = reinterpret_cast<T *>(ws + pl.off_refl2);
+  T *tau2 = reinterpret_cast<T *>(ws + pl.off_tau2);
+
+  for (int n = 0; n + 1 < N; ++n) {
+    const CorePlan &c = pl.core[n];
+    const int K1 = c.K1;
+    // (a) leaf: Y_n slabs and V-QR
+    if (n >= 1) {
+      // Q_n tree apply: root C at C1 level nlev (written by the previous SVD)
+      r = tree_apply(c.tree, c.R0, c.I, c.K1, nullptr, 0, dL + n, c.K0, C1,
+                     reinterpret_cast<double *>(ws + c.slot_off), B, st);
+      if (r) return r;
+    }
+    {
+      const int mode = n == 0 ? 1 : 0;
+      const SmemS2<T> m = smem_s2<T>(mode, n == 0 ? 1 : c.R0, K1, n == 0 ? 1 : c.K0, c.Tt, c.R1, 8);
+      S2Args<T> a{};
+      a.mode = mode;
+      a.g = Geom{c.I, c.P, c.Tt};
+      if (n >= 1) {
+        a.qrefl = reinterpret_cast<const T *>(ws + c.refl_off);
+        a.qtau = reinterpret_cast<const T *>(ws + c.tau_off);
+        a.b1 = c.R0;
+        a.Cleaf = C1 + c.tree.node_off[0] * (size_t)B * B;
+        a.ldc = B;
+        a.Lcur = dL + n;
+      } else {
+        a.b1 = 1;
+        a.X0 = reinterpret_cast<const T *>(x->cores[0]);
+        a.cin = c.R1;
+        a.Pm = N > 1 ? P1 : nullptr;
+        a.CC = 8;
+      }
+      a.K1 = K1;
+      a.vrefl = refl2;
+      a.vtau = tau2;
+      a.Rleaf = Rbase + c.tree.node_off[0] * (size_t)B * B;
+      a.oQ = m.oQ;
+      a.oCT = m.oCT;
+      a.oCR = m.oCR;
+      a.oRr = m.oRr;
+      a.oXs = m.oXs;
+      a.oPs = m.oPs;
+      a.oRed = m.oRed;
+      a.oW = m.oW;
+      a.oSc = m.oSc;
+      a.oTq = m.oTq;
+      a.oTv = m.oTv;
+      a.ldq = m.ldq;
+      a.ldv = m.ldv;
+      r = set_smem(k_s2_leaf<T>, m.bytes);
+      if (r) return r;
+      k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+      TT_CUDA(cudaGetLastError());
+    }
+    // (b) tree of V-QR factors (rows per slice = L[n])
+    r = tree_factor(c.tree, K1, c.I, 1, n == 0 ? nullptr : dL + n, Rbase, slots2, B, st);
+    if (r) return r;
+    // (c) SVD of the root, rank choice, U_hat -> C2 root, C_next -> C1 root of core n+1's tree
+    {
+      const CorePlan &cn = pl.core[n + 1];
+      SvdArgs a{};
+      a.Rroot = Rbase + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
+      a.K = K1;
+      a.In = c.I;
+      a.Lcur = dL + n;
+      a.Lnext = dL + n + 1;
+      a.n = n;
+      a.N = N;
+      a.eps = eps;
+      a.scal = dscal;
+      a.Uhat = C2 + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
+      a.Cnext = C1 + cn.tree.node_off[cn.tree.nlev] * (size_t)B * B;
+      a.ldu = B;
+      a.status = dstatus;
+      const size_t bytes = smem_svd(K1);
+      r = set_smem(k_svd, bytes);
+      if (r) return r;
+      k_svd<<<1, SVD_NT, bytes, st>>>(a);
+      TT_CUDA(cudaGetLastError());
+    }
+    // (d) U_hat down the V-QR tree, then the output core
+    r = tree_apply(c.tree, K1, c.I, 1, n == 0 ? nullptr : dL + n, 0, dL + n + 1, K1, C2, slots2, B, st);
+    if (r) return r;
+    {
+      const SmemOut<T> m = smem_out<T>(K1, n == 0 ? 1 : c.K0, c.Tt);
+      OutArgs<T> a{};
+      a.g = Geom{c.I, c.P, c.Tt};
+      a.vrefl = refl2;
+      a.vtau = tau2;
+      a.K1 = K1;
+      a.Lcur = dL + n;
+      a.Lnext = dL + n + 1;
+      a.Uleaf = C2 + c.tree.node_off[0] * (size_t)B * B;
+      a.ldc = B;
+      a.out = reinterpret_cast<T *>(out->cores[n]);
+      a.oV = m.oV;
+      a.oCT = m.oCT;
+      a.oCR = m.oCR;
+      a.oRed = m.oRed;
+      a.oW = m.oW;
+      a.oSc = m.oSc;
+      a.oTau = m.oTau;
+      a.ldv = m.ldv;
+      r = set_smem(k_s2_out<T>, m.bytes);
+      if (r) return r;
+      k_s2_out<T><<<c.P, NT, m.bytes, st>>>(a);
+      TT_CUDA(cudaGetLastError());
+    }
+  }
+  // last core: S_{N-2} x_1 Q_{N-1}
+  {
+    const CorePlan &c = pl.core[N - 1];
+    r = tree_apply(c.tree, c.R0, c.I, c.K1, nullptr, 0, dL + N - 1, c.K0, C1,
+                   reinterpret_cast<double *>(ws + c.slot_off), B, st);
+    if (r) return r;
+    const SmemS2<T> m = smem_s2<T>(2, c.R0, 1, c.K0, c.Tt, 1, 8);
+    S2Args<T> a{};
+    a.mode = 2;
+    a.g = Geom{c.I, c.P, c.Tt};
+    a.qrefl = reinterpret_cast<const T *>(ws + c.refl_off);
+    a.qtau = reinterpret_cast<const T *>(ws + c.tau_off);
+    a.b1 = c.R0;
+    a.K1 = 1;
+    a.Cleaf = C1 + c.tree.node_off[0] * (size_t)B * B;
+    a.ldc = B;
+    a.Lcur = dL + N - 1;
+    a.out = reinterpret_cast<T *>(out->cores[N - 1]);
+    a.oQ = m.oQ;
+    a.oCT = m.oCT;
+    a.oCR = m.oCR;
+    a.oRr = m.oRr;
+    a.oXs = m.oXs;
+    a.oPs = m.oPs;
+    a.oRed = m.oRed;
+    a.oW = m.oW;
+    a.oSc = m.oSc;
+    a.oTq = m.oTq;
+    a.oTv = m.oTv;
+    a.ldq = m.ldq;
+    a.ldv = m.ldv;
+    r = set_smem(k_s2_leaf<T>, m.bytes);
+    if (r) return r;
+    k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+    TT_CUDA(cudaGetLastError());
+  }
+  // ranks and status back to the host
+  std::vector<int> L(N + 1);
+  int status[4];
+  TT_CUDA(cudaMemcpyAsync(L.data(), dL, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaMemcpyAsync(status, dstatus, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  if (status[0]) return status[0];
+  for (int n = 0; n <= N; ++n) out->R[n] = L[n];
+  return TT_OK;
+}
+
+int round_run(const tt_tensor *x, double eps, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+  if (x->N == 1) {
+    const size_t es = x->dtype == TT_F64 ? 8 : 4;
+    TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDeviceToDevice, st));
+    TT_CUDA(cudaStreamSynchronize(st));
+    out->R[0] = out->R[1] = 1;
+    return TT_OK;
+  }
+  RoundPlan pl;
+  int r = x->dtype == TT_F64 ? make_plan<double>(x, pl) : make_plan<float>(x, pl);
+  if (r) return r;
+  if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
+  unsigned char *w = reinterpret_cast<unsigned char *>(ws);
+  return x->dtype == TT_F64 ? run_round<double>(pl, x, eps, out, w, st) : run_round<float>(pl, x, eps, out, w, st);
+}
+
+int norm_workspace(const tt_tensor *x, size_t *bytes) { return round_workspace(x, bytes); }
+
+template <typename T>
+static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, unsigned char *ws, cudaStream_t st) {
+  const int N = pl.N;
+  int r = N > 1 ? sweep1<T>(pl, x, ws, st) : TT_OK;
+  if (r) return r;
+  const CorePlan &c0 = pl.core[0];
+  double *part = reinterpret_cast<double *>(ws + pl.off_part);
+  double *res = reinterpret_cast<double *>(ws + pl.off_scal);
+  const double *Pm = N > 1 ? reinterpret_cast<const double *>(ws + pl.off_P) : nullptr;
+  const int K = N > 1 ? c0.K1 : 1;
+  const int cin = N > 1 ? c0.R1 : 1;
+  const int64_t total = c0.I * K;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (total + NT - 1) / NT));
+  k_push_sumsq<T><<<blocks, NT, 0, st>>>(reinterpret_cast<const T *>(x->cores[0]), c0.I, cin, K, Pm, part);
+  TT_CUDA(cudaGetLastError());
+  k_sum_sqrt<<<1, 32, 0, st>>>(part, blocks, res);
+  TT_CUDA(cudaGetLastError());
+  TT_CUDA(cudaMemcpyAsync(result, res, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TT_CUDA(cudaStreamSynchronize(st));
+  return TT_OK;
+}
+
+int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st) {
+  RoundPlan pl;
+  int r = x->dtype == TT_F64 ? make_plan<double>(x, pl) : make_plan<float>(x, pl);
+  if (r) return r;
+  if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
+  unsigned char *w = reinterpret_cast<unsigned char *>(ws);
+  return x->dtype == TT_F64 ? run_norm<double>(pl, x, result, w, st) : run_norm<float>(pl, x, result, w, st);
+}
+
+}  // namespace ttgb
