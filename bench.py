@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""TT-rounding throughput on GB300.
+
+Default workload (the plain-FP64 large-mode case): X = Y + Y', Y a random rank-16 TT
+with N = 10 modes of size I_n = 65536 (entries N(0,1)/sqrt(I_n R_{n-1})), Y' = 0.5 Y
++ 1e-9 Z taken core-wise, so X has formal ranks 32 (4.33 GB of FP64 cores) and is
+rounded at eps = 1e-8 back to ranks 16.  One step = one full TT rounding (both sweeps,
+every core) through the C ABI, inputs resident in HBM.  Inputs exceed L2 (129 MB), so
+no flush is needed between steps.
+
+  python bench.py [--gpus N --steps K --warmup W]          # this library
+  python bench.py --impl reference [...]                    # the FP64 CPU oracle
+
+Multi-GPU (torchrun): every rank rounds its own independent TT (seed + rank), no data
+collective; value = all ranks' rounds / max-over-ranks time ("weak" scaling).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TT-rounds/sec and HBM GB/s, mixed+batched vs plain FP64 on GB300 at rel err ≤1e-6"
+N_MODES, I_MODE, RANK, EPS = 10, 65536, 16, 1e-8
+SEED = 2011065302
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--modes", type=int, default=I_MODE, help="mode size I_n (default: the full 65536)")
+    return p.parse_args()
+
+
+def workload_desc(I):
+    return (f"plain-FP64 TT rounding, N={N_MODES}, I_n={I}, X = Y + (0.5Y + 1e-9Z) with rank-{RANK} Y, Z "
+            f"(formal ranks {2 * RANK}), eps={EPS:g}")
+
+
+def tt_bytes(I, R, es):
+    return sum(R[n] * I[n] * R[n + 1] for n in range(len(I))) * es
+
+
+# --------------------------------------------------------------------------------------
+# flop model (Sec. 3.5: TSQR 2mb^2, TRMM push, TSQR-Apply-Q 4mbc), per kernel class
+# --------------------------------------------------------------------------------------
+
+def flops_by_kernel(I, R, L):
+    """Algorithmic flops of one rounding, split like the library's kernel classes.
+    R: input ranks, L: output ranks."""
+    N = len(I)
+    K = [1] * (N + 1)
+    for n in range(N - 1, 0, -1):
+        K[n] = min(R[n], I[n] * K[n + 1])
+    f = {"s1_leaf": 0.0, "s2_leaf": 0.0, "s2_out": 0.0}
+    for n in range(N - 1, 0, -1):  # sweep 1: QR of H(X_n)^T (m = I K_{n+1} rows, b = R_n) + push of R_{n+1}
+        m, b = I[n] * K[n + 1], R[n]
+        f["s1_leaf"] += 2.0 * m * b * b + (m * b * R[n + 1] if n < N - 1 else 0.0)
+    for n in range(N - 1):  # sweep 2
+        if n >= 1:
+            f["s2_leaf"] += 4.0 * (I[n] * K[n + 1]) * R[n] * L[n]  # apply Q_n to S^T
+        else:
+            f["s2_leaf"] += 1.0 * I[0] * K[1] * R[1]  # push into core 0
+        f["s2_leaf"] += 2.0 * (L[n] * I[n]) * K[n + 1] ** 2  # QR of V(Y_n)
+        f["s2_out"] += 4.0 * (L[n] * I[n]) * K[n + 1] * L[n + 1]  # Q' U_hat
+    f["s2_leaf"] += 4.0 * (I[N - 1] * 1) * R[N - 1] * L[N - 1]  # last core
+    return f
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2011_06532_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_fp64_large_modes.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_sha") != source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------------------
+# clocks
+# --------------------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}", "--format=csv,noheader",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# --------------------------------------------------------------------------------------
+
+def oracle_sample_time(I_sample, seed):
+    import oracle
+    import ttgen
+
+    Y, Yp = ttgen.perturbed_pair([I_sample] * N_MODES, RANK, seed)
+    X = oracle.tt_add(Y, Yp)
+    t0 = time.perf_counter()
+    oracle.tt_round(X, EPS)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    total = args.steps + args.warmup
+    # per-step sample sized so the whole run stays within a few minutes (cost is linear in I_n)
+    I_sample = max(512, min(8192, int(65536 * 120.0 / (max(total, 1) * 115.0)) // 512 * 512))
+    times = []
+    for k in range(total):
+        t = oracle_sample_time(I_sample, SEED)
+        if k >= args.warmup:
+            times.append(t)
+    t_step = sum(times) / len(times)
+    value = (I_sample / args.modes) / t_step
+    sample = f"oracle tt_round of the same construction with I_n={I_sample} per step, scaled by {I_sample}/{args.modes}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TT-rounds/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3 * args.modes / I_sample,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(args.modes), "N": N_MODES, "I": args.modes, "formal_rank": 2 * RANK,
+                       "eps": EPS, "seed": SEED},
+            "cpu_baseline": {"value": value, "unit": "TT-rounds/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TT-rounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+# this library
+# --------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+    import ttgen
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ttgb.build()
+    dev = torch.device("cuda", local)
+    seed = SEED + 7919 * rank
+    I = [args.modes] * N_MODES
+    Y, Yp = ttgen.perturbed_pair(I, RANK, seed)
+    dY = ttgb.from_host(Y.I, Y.R, Y.cores, device=dev)
+    dYp = ttgb.from_host(Yp.I, Yp.R, Yp.cores, device=dev)
+    X = ttgb.tt_add(dY, dYp)  # formal ranks 32, built by the library's own sum kernel
+    del dY, dYp
+    torch.cuda.synchronize()
+    in_bytes = X.nbytes()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        out = ttgb.tt_round(X, EPS)
+    torch.cuda.synchronize()
+    L = out.R
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident timed region ----------------
+    clocks = ClockSampler(local)
+    barrier()
+    ttgb.trace(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = ttgb.tt_round(X, EPS)
+    e1.record(stream)
+    barrier()
+    ttgb.trace(False)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    tr = ttgb.trace_read()
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = sum(v[0] for v in tr.values())
+    out_bytes = out.nbytes()
+
+    # ---------------- end to end through the API, host buffers ----------------
+    hX = [c.to("cpu").pin_memory() for c in X.cores]
+    hOut = [torch.empty(s, dtype=torch.float64).pin_memory() for s in X.core_sizes()]
+    dX = [torch.empty_like(c) for c in X.cores]
+    barrier()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        for dc, hc in zip(dX, hX):
+            dc.copy_(hc, non_blocking=True)
+        h2d += sum(c.numel() * 8 for c in hX)
+        y = ttgb.tt_round(ttgb.DeviceTT(X.I, X.R, dX), EPS)
+        for k, c in enumerate(y.cores):
+            hOut[k][: c.numel()].copy_(c, non_blocking=True)
+            d2h += c.numel() * 8
+    e3.record(stream)
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    rounds_per_s = world * args.steps / (ms / 1e3)
+    fl = flops_by_kernel(I, X.R, L)
+    dom = max(("s1_leaf", "s2_leaf", "s2_out"), key=lambda k: tr[k][1])
+    n_dom, ms_dom = tr[dom]
+    flops_per_launch = fl[dom] * args.steps / max(n_dom, 1)
+    achieved = fl[dom] * args.steps / (ms_dom / 1e3) / 1e12 if ms_dom > 0 else None
+    traffic = read_traffic(dom)
+
+    # CPU baseline: the oracle on a bounded sample (1/8 of the slices), one thread
+    cpu = None
+    if world == 1:
+        I_s = min(8192, args.modes)
+        t_cpu = oracle_sample_time(I_s, SEED)
+        cpu = {"value": (I_s / args.modes) / t_cpu, "unit": "TT-rounds/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle tt_round of the same construction with I_n={I_s} ({t_cpu:.1f} s), "
+                         f"scaled by {I_s}/{args.modes} (cost is linear in I_n)"}
+
+    alg_bytes = 2 * in_bytes + out_bytes  # two reads of the input cores, one write of the output
+    line = {
+        "metric": METRIC, "value": rounds_per_s, "unit": "TT-rounds/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.modes), "N": N_MODES, "I": args.modes, "formal_rank": 2 * RANK,
+                   "eps": EPS, "seed": SEED, "output_ranks": L, "input_bytes": in_bytes,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "one independent TT per rank"},
+        "hbm_gbs": alg_bytes * rounds_per_s / world / 1e9,
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+                     "traffic": traffic, "flops_per_launch": flops_per_launch,
+                     "ms_per_launch": ms_dom / max(n_dom, 1),
+                     "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz"},
+        "kernel_ms_per_step": {k: v[1] / args.steps for k, v in tr.items() if v[0]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * args.steps / (ms_e2e / 1e3), "unit": "TT-rounds/s",
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

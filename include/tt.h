@@ -147,6 +147,38 @@ int tt_norm(const tt_tensor *x, double *result, void *workspace, size_t workspac
 /* Static description of a status code. */
 const char *tt_status_string(int status);
 
+/*
+ * Diagnostics (no counterpart in the paper): per kernel class, the number of
+ * kernels this library launched and, while tracing is on, their device time.
+ */
+typedef enum {
+  TT_K_S1_LEAF = 0,     /* right-to-left sweep: slab push + Householder QR (Alg. 6, first loop) */
+  TT_K_TREE_FACTOR = 1, /* reduction tree of triangular factors (TSQR, Alg. 3) */
+  TT_K_TREE_APPLY = 2,  /* root-to-leaf application of stored tree reflectors (Alg. 4) */
+  TT_K_S2_LEAF = 3,     /* left-to-right sweep: apply stored Q_n, QR of V(Y_n) slabs */
+  TT_K_S2_OUT = 4,      /* left-to-right sweep: output core Q' U_hat */
+  TT_K_SVD = 5,         /* FP64 Jacobi SVD of the root factor and rank choice */
+  TT_K_ADD = 6,
+  TT_K_HADAMARD = 7,
+  TT_K_DOT = 8,
+  TT_K_MISC = 9,        /* control-block set-up, norm reductions */
+  TT_K_COUNT = 10
+} tt_kernel_kind;
+
+/*
+ * enable != 0: reset all counters and start bracketing every launch with two
+ * CUDA events recorded on the launch's own stream; enable == 0: stop recording
+ * events (counters keep counting).  Not thread-safe with concurrent calls.
+ */
+int tt_trace(int enable);
+
+/*
+ * For kernel class `kind`: *launches = kernels launched since the last
+ * tt_trace(1); *milliseconds = summed device time of the launches recorded
+ * while tracing was on (waits for those events).  Either pointer may be NULL.
+ */
+int tt_trace_read(int kind, int64_t *launches, double *milliseconds);
+
 #ifdef __cplusplus
 }
 #endif

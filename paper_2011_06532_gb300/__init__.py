@@ -22,7 +22,7 @@ from . import _native
 from ._native import build  # noqa: F401  (re-export)
 
 __all__ = ["DeviceTT", "build", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard", "tt_dot", "tt_norm",
-           "TTError", "from_host", "to_host"]
+           "TTError", "from_host", "to_host", "trace", "trace_read"]
 
 _DTYPES = {torch.float64: 0, torch.float32: 1}
 
@@ -215,6 +215,23 @@ def tt_norm(x: DeviceTT, stream=None) -> float:
     _check(lib.tt_norm(d.ref, ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
                        _stream(stream)), "tt_norm")
     return float(res.value)
+
+
+def trace(enable: bool) -> None:
+    """Start (reset counters, bracket launches with CUDA events) or stop kernel tracing."""
+    _check(_native.load().tt_trace(1 if enable else 0), "tt_trace")
+
+
+def trace_read() -> dict:
+    """{kernel class: (launches, device milliseconds)} since the last trace(True)."""
+    lib = _native.load()
+    out = {}
+    for k, name in enumerate(_native.KERNEL_KINDS):
+        n = ctypes.c_int64(0)
+        ms = ctypes.c_double(0.0)
+        _check(lib.tt_trace_read(k, ctypes.byref(n), ctypes.byref(ms)), "tt_trace_read")
+        out[name] = (int(n.value), float(ms.value))
+    return out
 
 
 def from_host(I: Sequence[int], R: Sequence[int], cores: Sequence, dtype=torch.float64, device="cuda") -> DeviceTT:

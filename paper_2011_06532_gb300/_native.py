@@ -75,7 +75,9 @@ class TTTensor(ctypes.Structure):
 EXPORTS = [
     "tt_round_workspace_size", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard",
     "tt_dot_workspace_size", "tt_dot", "tt_norm_workspace_size", "tt_norm", "tt_status_string",
+    "tt_trace", "tt_trace_read",
 ]
+KERNEL_KINDS = ["s1_leaf", "tree_factor", "tree_apply", "s2_leaf", "s2_out", "svd", "add", "hadamard", "dot", "misc"]
 
 _lib = None
 
@@ -107,6 +109,10 @@ def load(path: str | None = None):
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.tt_trace.argtypes = [ctypes.c_int]
+    lib.tt_trace.restype = ctypes.c_int
+    lib.tt_trace_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    lib.tt_trace_read.restype = ctypes.c_int
     lib.tt_status_string.argtypes = [ctypes.c_int]
     lib.tt_status_string.restype = ctypes.c_char_p
     if path is None:

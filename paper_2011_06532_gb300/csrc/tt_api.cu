@@ -3,6 +3,10 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+#include <vector>
+
 #include "tt.h"
 #include "tt_engine.h"
 
@@ -43,7 +47,79 @@ cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+namespace ttgb {
+
+namespace {
+struct TraceState {
+  std::atomic<int64_t> launches[TT_K_COUNT];
+  std::atomic<bool> on{false};
+  std::mutex mu;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events[TT_K_COUNT];
+};
+TraceState &trace_state() {
+  static TraceState s;
+  return s;
+}
+}  // namespace
+
+TraceScope::TraceScope(int k, cudaStream_t s) : kind(k), st(s) {
+  TraceState &ts = trace_state();
+  ts.launches[kind].fetch_add(1);
+  if (ts.on.load()) {
+    if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e0, st);
+    } else {
+      e0 = e1 = nullptr;
+    }
+  }
+}
+
+TraceScope::~TraceScope() {
+  if (!e0 || !e1) return;
+  cudaEventRecord(e1, st);
+  TraceState &ts = trace_state();
+  std::lock_guard<std::mutex> g(ts.mu);
+  ts.events[kind].emplace_back(e0, e1);
+}
+
+}  // namespace ttgb
+
 extern "C" {
+
+int tt_trace(int enable) {
+  ttgb::TraceState &ts = ttgb::trace_state();
+  std::lock_guard<std::mutex> g(ts.mu);
+  if (enable) {
+    for (int k = 0; k < TT_K_COUNT; ++k) {
+      ts.launches[k].store(0);
+      for (auto &p : ts.events[k]) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+      }
+      ts.events[k].clear();
+    }
+  }
+  ts.on.store(enable != 0);
+  return TT_OK;
+}
+
+int tt_trace_read(int kind, int64_t *launches, double *milliseconds) {
+  if (kind < 0 || kind >= TT_K_COUNT) return TT_ERR_INVALID_ARG;
+  ttgb::TraceState &ts = ttgb::trace_state();
+  std::lock_guard<std::mutex> g(ts.mu);
+  if (launches) *launches = ts.launches[kind].load();
+  if (milliseconds) {
+    double sum = 0.0;
+    for (auto &p : ts.events[kind]) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(p.second) != cudaSuccess) return TT_ERR_CUDA;
+      if (cudaEventElapsedTime(&ms, p.first, p.second) != cudaSuccess) return TT_ERR_CUDA;
+      sum += ms;
+    }
+    *milliseconds = sum;
+  }
+  return TT_OK;
+}
 
 int tt_round_workspace_size(const tt_tensor *x, size_t *bytes) {
   if (!valid_tensor(x) || !bytes) return TT_ERR_INVALID_ARG;

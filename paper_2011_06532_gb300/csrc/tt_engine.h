@@ -18,4 +18,13 @@ int hadamard_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStr
 int dot_workspace(const tt_tensor *a, const tt_tensor *b, size_t *bytes);
 int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, size_t ws_bytes, cudaStream_t st);
 
+// Counts a launch of `kind` and, while tracing is on, brackets it with CUDA events on st.
+struct TraceScope {
+  TraceScope(int kind, cudaStream_t st);
+  ~TraceScope();
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
 }  // namespace ttgb

@@ -67,6 +67,7 @@ int add_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStream_t
     const int rs = n == 0 ? 0 : ra0;      // row offset of the B block
     const int cs = n == N - 1 ? 0 : ra1;  // column offset of the B block
     const int64_t total = out->R[n] * a->I[n] * out->R[n + 1];
+    TraceScope ts_(TT_K_ADD, st);
     if (a->dtype == TT_F64)
       k_add_core<double><<<grid_for(total), 256, 0, st>>>((const double *)a->cores[n], (const double *)b->cores[n],
                                                             (double *)out->cores[n], a->I[n], ra0, ra1, rb0, rb1, rs,
@@ -105,6 +106,7 @@ int hadamard_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStr
   for (int n = 0; n < N; ++n) {
     const int ra0 = (int)a->R[n], ra1 = (int)a->R[n + 1], rb0 = (int)b->R[n], rb1 = (int)b->R[n + 1];
     const int64_t total = out->R[n] * a->I[n] * out->R[n + 1];
+    TraceScope ts_(TT_K_HADAMARD, st);
     if (a->dtype == TT_F64)
       k_hadamard_core<double><<<grid_for(total), 256, 0, st>>>((const double *)a->cores[n],
                                                                  (const double *)b->cores[n], (double *)out->cores[n],
@@ -193,7 +195,10 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
   double *W0 = reinterpret_cast<double *>(ws);
   double *W1 = W0 + maxw;
   double *part = W1 + maxw;
-  k_dot_init<<<1, 32, 0, st>>>(W0);
+  {
+    TraceScope ts_(TT_K_MISC, st);
+    k_dot_init<<<1, 32, 0, st>>>(W0);
+  }
   TT_CUDA(cudaGetLastError());
   for (int n = 0; n < a->N; ++n) {
     const int rx0 = (int)a->R[n], rx1 = (int)a->R[n + 1], ry0 = (int)b->R[n], ry1 = (int)b->R[n + 1];
@@ -201,6 +206,7 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
     const size_t es = a->dtype == TT_F64 ? 8 : 4;
     const size_t smem = ((es * (size_t)(ry0 * rx0 + ry0 * rx1) + 15) / 16) * 16 + sizeof(double) * ry1 * rx1;
     if (smem > 220 * 1024) return TT_ERR_UNSUPPORTED;
+    TraceScope ts_(TT_K_DOT, st);
     if (a->dtype == TT_F64) {
       if (smem > 48 * 1024)
         TT_CUDA(cudaFuncSetAttribute(k_dot_core<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -213,7 +219,10 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
                                                  rx1, ry0, ry1, W0, part);
     }
     TT_CUDA(cudaGetLastError());
-    k_dot_reduce<<<(ry1 * rx1 + 255) / 256, 256, 0, st>>>(part, nb, ry1 * rx1, W1);
+    {
+      TraceScope ts_(TT_K_DOT, st);
+      k_dot_reduce<<<(ry1 * rx1 + 255) / 256, 256, 0, st>>>(part, nb, ry1 * rx1, W1);
+    }
     TT_CUDA(cudaGetLastError());
     std::swap(W0, W1);
   }

@@ -1035,7 +1035,10 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
     a.oW = sm.oW;
     a.oSc = sm.oSc;
     a.oTau = sm.oTau;
-    k_tree_factor<<<tr.count[l + 1], NT, sm.bytes, st>>>(a);
+    {
+      TraceScope ts_(TT_K_TREE_FACTOR, st);
+      k_tree_factor<<<tr.count[l + 1], NT, sm.bytes, st>>>(a);
+    }
     TT_CUDA(cudaGetLastError());
   }
   return TT_OK;
@@ -1087,7 +1090,10 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
     a.oW = use.oW;
     a.oSc = use.oSc;
     a.oTau = use.oTau;
-    k_tree_apply<<<tr.count[l], NT, use.bytes, st>>>(a);
+    {
+      TraceScope ts_(TT_K_TREE_APPLY, st);
+      k_tree_apply<<<tr.count[l], NT, use.bytes, st>>>(a);
+    }
     TT_CUDA(cudaGetLastError());
   }
   return TT_OK;
@@ -1124,7 +1130,10 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     a.ldt = m.ldt;
     int r = set_smem(k_s1_leaf<T>, m.bytes);
     if (r) return r;
-    k_s1_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+    {
+      TraceScope ts_(TT_K_S1_LEAF, st);
+      k_s1_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+    }
     TT_CUDA(cudaGetLastError());
     r = tree_factor(c.tree, c.R0, c.I, c.K1, nullptr, Rbase, reinterpret_cast<double *>(ws + c.slot_off), B, st);
     if (r) return r;
@@ -1148,7 +1157,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   double *dscal = reinterpret_cast<double *>(ws + pl.off_scal);
   int *dstatus = reinterpret_cast<int *>(ws + pl.off_status);
   // L[0] = L[N] = 1 are fixed; the others are written by the SVD kernels
-  k_init_ctl<<<1, 32, 0, st>>>(dL, N, dstatus);
+  {
+    TraceScope ts_(TT_K_MISC, st);
+    k_init_ctl<<<1, 32, 0, st>>>(dL, N, dstatus);
+  }
   TT_CUDA(cudaGetLastError());
   int r = sweep1<T>(pl, x, ws, st);
   if (r) return r;
@@ -1209,7 +1221,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.ldv = m.ldv;
       r = set_smem(k_s2_leaf<T>, m.bytes);
       if (r) return r;
-      k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+      {
+        TraceScope ts_(TT_K_S2_LEAF, st);
+        k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+      }
       TT_CUDA(cudaGetLastError());
     }
     // (b) tree of V-QR factors (rows per slice = L[n])
@@ -1235,7 +1250,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       const size_t bytes = smem_svd(K1);
       r = set_smem(k_svd, bytes);
       if (r) return r;
-      k_svd<<<1, SVD_NT, bytes, st>>>(a);
+      {
+        TraceScope ts_(TT_K_SVD, st);
+        k_svd<<<1, SVD_NT, bytes, st>>>(a);
+      }
       TT_CUDA(cudaGetLastError());
     }
     // (d) U_hat down the V-QR tree, then the output core
@@ -1263,7 +1281,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.ldv = m.ldv;
       r = set_smem(k_s2_out<T>, m.bytes);
       if (r) return r;
-      k_s2_out<T><<<c.P, NT, m.bytes, st>>>(a);
+      {
+        TraceScope ts_(TT_K_S2_OUT, st);
+        k_s2_out<T><<<c.P, NT, m.bytes, st>>>(a);
+      }
       TT_CUDA(cudaGetLastError());
     }
   }
@@ -1300,7 +1321,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     a.ldv = m.ldv;
     r = set_smem(k_s2_leaf<T>, m.bytes);
     if (r) return r;
-    k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+    {
+      TraceScope ts_(TT_K_S2_LEAF, st);
+      k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+    }
     TT_CUDA(cudaGetLastError());
   }
   // ranks and status back to the host
@@ -1345,9 +1369,15 @@ static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, uns
   const int cin = N > 1 ? c0.R1 : 1;
   const int64_t total = c0.I * K;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (total + NT - 1) / NT));
-  k_push_sumsq<T><<<blocks, NT, 0, st>>>(reinterpret_cast<const T *>(x->cores[0]), c0.I, cin, K, Pm, part);
+  {
+    TraceScope ts_(TT_K_MISC, st);
+    k_push_sumsq<T><<<blocks, NT, 0, st>>>(reinterpret_cast<const T *>(x->cores[0]), c0.I, cin, K, Pm, part);
+  }
   TT_CUDA(cudaGetLastError());
-  k_sum_sqrt<<<1, 32, 0, st>>>(part, blocks, res);
+  {
+    TraceScope ts_(TT_K_MISC, st);
+    k_sum_sqrt<<<1, 32, 0, st>>>(part, blocks, res);
+  }
   TT_CUDA(cudaGetLastError());
   TT_CUDA(cudaMemcpyAsync(result, res, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CUDA(cudaStreamSynchronize(st));

@@ -55,25 +55,46 @@ def philox4x32_10(ctr: np.ndarray, key: Sequence[int]) -> np.ndarray:
     return np.stack([c0, c1, c2, c3], axis=1).astype(np.uint32)
 
 
-def normals(count: int, seed: int, stream: int, core: int) -> np.ndarray:
-    """`count` standard normals (FP64) for one (seed, stream, core) triple."""
-    pairs = (count + 1) // 2
-    idx = np.arange(pairs, dtype=np.uint64)
-    ctr = np.empty((pairs, 4), dtype=np.uint32)
+def _normal_pairs(p0: int, p1: int, seed: int, stream: int, core: int, out: np.ndarray) -> None:
+    """Fills out[2*p0 : 2*p1] with the normals of counter values p0..p1-1."""
+    idx = np.arange(p0, p1, dtype=np.uint64)
+    ctr = np.empty((p1 - p0, 4), dtype=np.uint32)
     ctr[:, 0] = (idx & _MASK32).astype(np.uint32)
     ctr[:, 1] = (idx >> np.uint64(32)).astype(np.uint32)
     ctr[:, 2] = np.uint32(core & 0xFFFFFFFF)
     ctr[:, 3] = 0
-    out = philox4x32_10(ctr, (seed & 0xFFFFFFFF, stream & 0xFFFFFFFF)).astype(np.uint64)
-    a = (out[:, 0] << np.uint64(32)) | out[:, 1]
-    b = (out[:, 2] << np.uint64(32)) | out[:, 3]
+    r = philox4x32_10(ctr, (seed & 0xFFFFFFFF, stream & 0xFFFFFFFF)).astype(np.uint64)
+    a = (r[:, 0] << np.uint64(32)) | r[:, 1]
+    b = (r[:, 2] << np.uint64(32)) | r[:, 3]
     u1 = ((a >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)  # (0, 1]
     u2 = (b >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)  # [0, 1)
     rad = np.sqrt(-2.0 * np.log(u1))
     th = 2.0 * np.pi * u2
+    out[2 * p0:2 * p1:2] = rad * np.cos(th)
+    out[2 * p0 + 1:2 * p1:2] = rad * np.sin(th)
+
+
+_CHUNK = 1 << 19
+
+
+def normals(count: int, seed: int, stream: int, core: int) -> np.ndarray:
+    """`count` standard normals (FP64) for one (seed, stream, core) triple.
+
+    Large requests are split by counter range over host threads; the values do
+    not depend on the split.
+    """
+    pairs = (count + 1) // 2
     z = np.empty(2 * pairs, dtype=np.float64)
-    z[0::2] = rad * np.cos(th)
-    z[1::2] = rad * np.sin(th)
+    bounds = [(p, min(p + _CHUNK, pairs)) for p in range(0, pairs, _CHUNK)]
+    if len(bounds) <= 1:
+        for p0, p1 in bounds:
+            _normal_pairs(p0, p1, seed, stream, core, z)
+    else:
+        import concurrent.futures
+        import os
+
+        with concurrent.futures.ThreadPoolExecutor(min(len(bounds), os.cpu_count() or 1)) as ex:
+            list(ex.map(lambda b: _normal_pairs(b[0], b[1], seed, stream, core, z), bounds))
     return z[:count]
 
 
