@@ -133,6 +133,36 @@ int tt_dot_workspace_size(const tt_tensor *a, const tt_tensor *b, size_t *bytes)
 int tt_dot(const tt_tensor *a, const tt_tensor *b, double *result, void *workspace, size_t workspace_bytes,
            void *stream);
 
+/*
+ * Size of the fixed device scratch array behind tt_dot_noalloc (8 MiB).
+ */
+#define TT_DOT_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+
+/*
+ * tt_dot without any memory allocation, for callers that cannot allocate
+ * device memory: code whose host framework owns every device allocation (a
+ * fixed pool or arena it does not expose), loops where the device-wide
+ * synchronization of cudaMalloc/cudaFree is not acceptable, or embedded and
+ * plugin contexts where allocating is forbidden.  The paper has no counterpart:
+ * this is the same inner product as tt_dot (same kernels, same result) with its
+ * scratch taken from a fixed array of TT_DOT_NOALLOC_SCRATCH_BYTES that lives in
+ * device memory of every GPU that loads this library, until the process exits.
+ *
+ * a, b, result and stream as in tt_dot; no workspace argument.  Neither this
+ * routine nor anything it calls allocates (no cudaMalloc, cudaFree or
+ * allocating library call).  Returns TT_ERR_UNSUPPORTED, having queued nothing,
+ * when the scratch tt_dot would need (tt_dot_workspace_size(a, b), about
+ * 8 (2 max_n Ra[n]Rb[n] + max_n min(I[n], 304) Ra[n+1]Rb[n+1]) bytes) exceeds
+ * TT_DOT_NOALLOC_SCRATCH_BYTES; two tensors whose ranks are all r fit for
+ * r <= 58.
+ * The first call on a device looks up that device's scratch address, with the
+ * device current; make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents (every value a call
+ * reads it writes first): calls whose work overlaps on the GPU -- other streams,
+ * other host threads -- race and give wrong results.  Synchronizes `stream`.
+ */
+int tt_dot_noalloc(const tt_tensor *a, const tt_tensor *b, double *result, void *stream);
+
 /* Workspace bytes tt_norm needs for input x. */
 int tt_norm_workspace_size(const tt_tensor *x, size_t *bytes);
 

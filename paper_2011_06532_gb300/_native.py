@@ -75,7 +75,7 @@ class TTTensor(ctypes.Structure):
 EXPORTS = [
     "tt_round_workspace_size", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard",
     "tt_dot_workspace_size", "tt_dot", "tt_norm_workspace_size", "tt_norm", "tt_status_string",
-    "tt_trace", "tt_trace_read",
+    "tt_trace", "tt_trace_read", "tt_dot_noalloc",
 ]
 KERNEL_KINDS = ["s1_leaf", "tree_factor", "tree_apply", "s2_leaf", "s2_out", "svd", "add", "hadamard", "dot", "misc"]
 
@@ -102,6 +102,7 @@ def load(path: str | None = None):
         "tt_hadamard": [T, T, T, vp],
         "tt_dot_workspace_size": [T, T, sz],
         "tt_dot": [T, T, dp, vp, ctypes.c_size_t, vp],
+        "tt_dot_noalloc": [T, T, dp, vp],
         "tt_norm_workspace_size": [T, sz],
         "tt_norm": [T, dp, vp, ctypes.c_size_t, vp],
     }

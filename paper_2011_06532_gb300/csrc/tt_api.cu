@@ -173,6 +173,11 @@ int tt_dot(const tt_tensor *a, const tt_tensor *b, double *result, void *workspa
   return ttgb::dot_run(a, b, result, workspace, workspace_bytes, as_stream(stream));
 }
 
+int tt_dot_noalloc(const tt_tensor *a, const tt_tensor *b, double *result, void *stream) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !result) return TT_ERR_INVALID_ARG;
+  return ttgb::dot_noalloc_run(a, b, result, as_stream(stream));
+}
+
 int tt_norm_workspace_size(const tt_tensor *x, size_t *bytes) {
   if (!valid_tensor(x) || !bytes) return TT_ERR_INVALID_ARG;
   if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;

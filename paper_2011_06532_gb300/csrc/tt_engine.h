@@ -17,6 +17,7 @@ int add_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStream_t
 int hadamard_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStream_t st);
 int dot_workspace(const tt_tensor *a, const tt_tensor *b, size_t *bytes);
 int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, size_t ws_bytes, cudaStream_t st);
+int dot_noalloc_run(const tt_tensor *a, const tt_tensor *b, double *result, cudaStream_t st);
 
 // Counts a launch of `kind` and, while tracing is on, brackets it with CUDA events on st.
 struct TraceScope {

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tt.h"
 #include "tt_engine.h"
@@ -229,6 +230,49 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
   TT_CUDA(cudaMemcpyAsync(result, W0, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CUDA(cudaStreamSynchronize(st));
   return TT_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// inner product without any allocation: scratch in a fixed device array
+// ------------------------------------------------------------------------------------
+
+// Scratch of tt_dot_noalloc: every process that loads this library holds this array on
+// every device it uses, until exit.  It is shared by all calls (no per-call state).
+static __device__ __align__(256) double g_dot_scratch[TT_DOT_NOALLOC_SCRATCH_BYTES / sizeof(double)];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double *g_scratch_ptr[kMaxDevices] = {nullptr};
+}  // namespace
+
+// Device address of g_dot_scratch for the current device.  The first call on a device
+// looks it up (host code cannot use the symbol itself: in host code it names a host-side
+// stand-in, not device memory).
+static int dot_scratch_ptr(double **out) {
+  int dev = 0;
+  TT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return TT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    TT_CUDA(cudaGetSymbolAddress(&p, g_dot_scratch));
+    g_scratch_ptr[dev] = static_cast<double *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return TT_OK;
+}
+
+int dot_noalloc_run(const tt_tensor *a, const tt_tensor *b, double *result, cudaStream_t st) {
+  size_t need = 0;
+  dot_workspace(a, b, &need);
+  if (need > TT_DOT_NOALLOC_SCRATCH_BYTES) return TT_ERR_UNSUPPORTED;
+  double *scratch = nullptr;
+  const int r = dot_scratch_ptr(&scratch);
+  if (r) return r;
+  // W0 is set by the first kernel and every partial sum is written before it is read,
+  // so nothing left by an earlier call needs clearing.
+  return dot_run(a, b, result, scratch, TT_DOT_NOALLOC_SCRATCH_BYTES, st);
 }
 
 }  // namespace ttgb
