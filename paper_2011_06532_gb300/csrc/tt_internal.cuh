@@ -96,15 +96,24 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
 // 0..k-1 hold updated R rows; tile entries (r, c) with c < k + r hold reflector entries
 // and, for r < kk - k, entries c >= k + r hold R row k + r.  tau[0..kk-1] is written.
 // Rr and tile are row-major with leading dimensions ldr, ldt.  Returns kk.
+// tri_off >= 0 declares the tile upper trapezoidal with row r starting at column
+// r + tri_off (a triangular factor stacked under Rr): reflector j then only touches tile
+// rows r <= j - tri_off, the others being zero in column j.  tri_off < 0: dense tile.
+__device__ __forceinline__ int tile_rows_for(int j, int M, int tri_off) {
+  return tri_off < 0 ? M : min(M, max(0, j - tri_off + 1));
+}
+
 template <typename T>
-__device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s) {
+__device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+                         int tri_off = -1) {
   const int kk = min(k + M, b);
   for (int j = 0; j < kk; ++j) {
     const int r0 = j < k ? 0 : j - k + 1;
+    const int Mj = tile_rows_for(j, M, tri_off);
     T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
     if (threadIdx.x < 32) {
       T ss = T(0);
-      for (int r = r0 + threadIdx.x; r < M; r += 32) {
+      for (int r = r0 + threadIdx.x; r < Mj; r += 32) {
         const T v = tile[(size_t)r * ldt + j];
         ss += v * v;
       }
@@ -115,8 +124,12 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
           const T alpha = piv[j];
           const T nrm = tsqrt(alpha * alpha + ss);
           const T beta = alpha >= T(0) ? -nrm : nrm;
-          tj = (beta - alpha) / beta;
-          scale = T(1) / (alpha - beta);
+          // one division: with d = alpha - beta and q = 1 / (beta d),
+          // tau = (beta - alpha) / beta = -d d q and 1 / d = beta q
+          const T d = alpha - beta;
+          const T q = T(1) / (beta * d);
+          tj = -d * d * q;
+          scale = beta * q;
           piv[j] = beta;
         }
         tau[j] = tj;
@@ -128,9 +141,9 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
     const T tj = s.sc[1];
     if (tj != T(0)) {
       const T scale = s.sc[0];
-      for (int r = r0 + threadIdx.x; r < M; r += NT) tile[(size_t)r * ldt + j] *= scale;
+      for (int r = r0 + threadIdx.x; r < Mj; r += NT) tile[(size_t)r * ldt + j] *= scale;
       __syncthreads();
-      reflect(tj, tile + j, ldt, r0, M, piv + j + 1, tile + j + 1, ldt, b - j - 1, s);
+      reflect(tj, tile + j, ldt, r0, Mj, piv + j + 1, tile + j + 1, ldt, b - j - 1, s);
     } else {
       __syncthreads();
     }
@@ -153,17 +166,17 @@ __device__ void hh_take_rows(T *Rr, int ldr, int k, int kk, const T *tile, int l
 // Applies the orthogonal factor of one hh_factor step, Q_t = H_0 ... H_{kk-1}, to the
 // stacked block [CR (k rows); CT (M rows)] of nc columns (row-major, leading dims ldcr,
 // ldct): reflectors are applied from kk-1 down to 0.  V / tau are the stored tile and
-// tau of that step (V row-major, ld ldv).
+// tau of that step (V row-major, ld ldv); tri_off as in hh_factor.
 template <typename T>
 __device__ void hh_apply(const T *V, int ldv, const T *tau, int k, int M, int b, T *CR, int ldcr, T *CT, int ldct,
-                         int nc, Scratch<T> s) {
+                         int nc, Scratch<T> s, int tri_off = -1) {
   const int kk = min(k + M, b);
   for (int j = kk - 1; j >= 0; --j) {
     const T tj = tau[j];
     if (tj == T(0)) continue;
     const int r0 = j < k ? 0 : j - k + 1;
     T *piv = j < k ? CR + (size_t)j * ldcr : CT + (size_t)(j - k) * ldct;
-    reflect(tj, V + j, ldv, r0, M, piv, CT, ldct, nc, s);
+    reflect(tj, V + j, ldv, r0, tile_rows_for(j, M, tri_off), piv, CT, ldct, nc, s);
   }
 }
 

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(NT) k_tree_factor(TreeArgs a) {
         tile[r * a.lda + col] = Rc[(size_t)(ra + r) * b + col];
       }
       __syncthreads();
-      const int kk = hh_factor(Rr, b, k, tile, a.lda, M, b, taus, s);
+      const int kk = hh_factor(Rr, b, k, tile, a.lda, M, b, taus, s, ra);
       for (int idx = t; idx < M * b; idx += NT) {
         const int r = idx / b, col = idx - r * b;
         slot[(size_t)(ra + r) * b + col] = tile[r * a.lda + col];
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
         CT[r * nc + col] = (kb + r < ka) ? C[(kb + r) * nc + col] : 0.0;
       }
       __syncthreads();
-      hh_apply(V, a.lda, taus, kb, M, b, C, nc, CT, nc, nc, s);
+      hh_apply(V, a.lda, taus, kb, M, b, C, nc, CT, nc, nc, s, ra);
       __syncthreads();
       for (int idx = t; idx < M * nc; idx += NT) {
         const int r = idx / nc, col = idx - r * nc;
@@ -684,9 +684,10 @@ __global__ void k_sum_sqrt(const double *partial, int n, double *out) {
 
 namespace {
 
-constexpr int kG = 8;          // tree fan-in
+constexpr int kG = 2;          // tree fan-in (binary: fewest serial reflectors per root)
 constexpr int kMaxLev = 10;
 constexpr size_t kSmemBudget = 220 * 1024;
+constexpr size_t kSmemPair = 110 * 1024;  // two co-resident leaf CTAs per SM
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -715,7 +716,7 @@ Tree make_tree(int P) {
   tr.count[0] = P;
   tr.lpc[0] = 1;
   int l = 0;
-  while (tr.count[l] > 1) {
+  while (tr.count[l] > 1 && l < kMaxLev) {
     tr.count[l + 1] = (tr.count[l] + kG - 1) / kG;
     tr.lpc[l + 1] = tr.lpc[l] * kG;
     ++l;
@@ -736,7 +737,7 @@ Tree make_tree(int P) {
 }
 
 int leaves_for(int64_t I, int nsm) {
-  const int64_t target = 2 * (int64_t)nsm;
+  const int64_t target = std::min<int64_t>(2 * (int64_t)nsm, (int64_t)1 << kMaxLev);  // the tree holds 2^kMaxLev
   return (int)std::max<int64_t>(1, std::min<int64_t>(I, target));
 }
 
@@ -915,6 +916,25 @@ static bool choose_tiles(RoundPlan &pl) {
     }
     if (best == 0) return false;
     c.Tt = best;
+    // largest tile whose footprint still lets two leaf CTAs share an SM
+    for (int Tt = best; Tt >= 1; --Tt) {
+      size_t mx = 0;
+      if (n >= 1) {
+        mx = smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC).bytes;
+        if (n < N - 1) {
+          mx = std::max(mx, smem_s2<T>(0, c.R0, c.K1, c.K0, Tt, 1, CC).bytes);
+          mx = std::max(mx, smem_out<T>(c.K1, c.K0, Tt).bytes);
+        } else {
+          mx = std::max(mx, smem_s2<T>(2, c.R0, c.K1, c.K0, Tt, 1, CC).bytes);
+        }
+      } else {
+        mx = std::max(smem_s2<T>(1, 1, c.K1, 1, Tt, c.R1, CC).bytes, smem_out<T>(c.K1, 1, Tt).bytes);
+      }
+      if (mx <= kSmemPair) {
+        c.Tt = Tt;
+        break;
+      }
+    }
   }
   return true;
 }
