@@ -27,6 +27,42 @@ __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
 
+// FP64 reciprocal and reciprocal square root by Newton-Raphson iteration from a
+// single-precision hardware seed.  On GB300 every FP64 instruction occupies an SMSP's
+// FP64 unit for about 64 cycles and the FP64 divide / square root sequences take about
+// 650-700 cycles; these take about 8 FP64 instructions.  The argument is first scaled by
+// a power of two (exponent arithmetic on the bit pattern) into [1, 2) resp. [1, 4) so the
+// seed never under- or overflows; two Newton steps take the seed's ~2^-22 relative error
+// below FP64 rounding.  Valid for finite, normal, nonzero x (x > 0 for rsqrt_nr).
+__device__ __forceinline__ double rcp_nr(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
+  const double m = __longlong_as_double(bits - ((long long)ex << 52));  // |m| in [1, 2)
+  double y = (double)__frcp_rn((float)m);
+  // y <- y (2 - m y), written as y + y (1 - m y)
+  double e = fma(-m, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-m, y, 1.0);
+  y = fma(y, e, y);
+  return __longlong_as_double(__double_as_longlong(y) - ((long long)ex << 52));
+}
+
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
+  const int k = ex >> 1;  // floor(ex / 2)
+  const double m = __longlong_as_double(bits - ((long long)(2 * k) << 52));  // in [1, 4)
+  double y = (double)rsqrtf((float)m);
+  const double hm = 0.5 * m;
+  // y <- y (3 - m y^2) / 2
+  y = y * fma(-hm, y * y, 1.5);
+  y = y * fma(-hm, y * y, 1.5);
+  return __longlong_as_double(__double_as_longlong(y) - ((long long)k << 52));
+}
+
+// x in the range where the Newton helpers apply (normal, far from overflow)
+__device__ __forceinline__ bool nr_range(double x) { return x > 1e-290 && x < 1e290; }
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -122,12 +158,23 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
         T tj = T(0), scale = T(0);
         if (ss != T(0)) {
           const T alpha = piv[j];
-          const T nrm = tsqrt(alpha * alpha + ss);
-          const T beta = alpha >= T(0) ? -nrm : nrm;
-          // one division: with d = alpha - beta and q = 1 / (beta d),
+          const T v = alpha * alpha + ss;
+          T nrm, q;
+          // one reciprocal: with d = alpha - beta and q = 1 / (beta d),
           // tau = (beta - alpha) / beta = -d d q and 1 / d = beta q
+          if (sizeof(T) == 8 && nr_range((double)v)) {
+            nrm = (T)((double)v * rsqrt_nr((double)v));
+          } else {
+            nrm = tsqrt(v);
+          }
+          const T beta = alpha >= T(0) ? -nrm : nrm;
           const T d = alpha - beta;
-          const T q = T(1) / (beta * d);
+          const T bd = beta * d;
+          if (sizeof(T) == 8 && nr_range(fabs((double)bd))) {
+            q = (T)rcp_nr((double)bd);
+          } else {
+            q = T(1) / bd;
+          }
           tj = -d * d * q;
           scale = beta * q;
           piv[j] = beta;

@@ -127,6 +127,7 @@ struct SvdArgs {
   double *Cnext;        // K x K (ld ldu)
   int ldu;
   int *status;
+  int precond;          // run the FP32 pre-sweeps (shared memory permitting)
 };
 
 // ------------------------------------------------------------------------------------
@@ -484,41 +485,70 @@ __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<T> a) {
 }
 
 // ------------------------------------------------------------------------------------
-// FP64 one-sided Jacobi SVD of the root factor + rank choice (one CTA)
+// SVD of the root factor + rank choice (one CTA)
+//
+// One-sided Jacobi (Hestenes) with a round-robin pair ordering, one warp per pair.
+// When shared memory allows, an FP32 pass first rotates a scaled FP32 copy until its
+// columns are orthogonal to FP32 accuracy; its rotation matrix is re-orthonormalized in
+// FP64 (Newton-Schulz, V <- V (3I - V^T V) / 2, twice) and applied, B = A V, so the FP64
+// sweeps that follow start from nearly orthogonal columns and need few sweeps.  The FP64
+// sweeps use the same convergence test as a plain one-sided Jacobi
+// (|b_p^T b_q| <= tol ||b_p|| ||b_q||), so the singular values keep FP64 accuracy.
 // ------------------------------------------------------------------------------------
 
 constexpr int SVD_NT = 512;
 
-__global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int K = a.K, t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
-  const int Lc = *a.Lcur;
-  const int kroot = (int)min64((int64_t)Lc * a.In, K);
-  const bool wide = kroot < K;
-  const int ms = K, ns = wide ? kroot : K;  // A is ms x ns, column-major
-  double *A = reinterpret_cast<double *>(smem);
-  double *Vm = A + (size_t)ms * ns;
-  double *sig = Vm + (size_t)ns * ns;
-  int *pos = reinterpret_cast<int *>(sig + ns);  // 2 * (ns + 1)
-  int *ord = pos + 2 * (ns + 2);
-  int *flag = ord + ns + 1;
-  for (int idx = t; idx < ms * ns; idx += SVD_NT) {
-    const int c = idx / ms, r = idx - c * ms;
-    A[idx] = wide ? a.Rroot[(size_t)c * K + r] : a.Rroot[(size_t)r * K + c];
+// rotation [c s; -s c] zeroing the (p, q) entry of the 2x2 Gram [[al, ga], [ga, be]]:
+// with h = be - al, g = 2 ga, r = sqrt(h^2 + g^2): c = sqrt((|h| + r) / (2r)),
+// s = sign(h) g / sqrt(2r (|h| + r)) -- the smaller-angle solution t = s / c of
+// t^2 + 2 (h / g) t - 1 = 0; h = 0 takes t = 1.
+__device__ __forceinline__ void jrot(double al, double be, double ga, double &c, double &sn) {
+  const double h = be - al, g = 2.0 * ga;
+  if (h == 0.0) {
+    c = sn = 0.70710678118654752;
+    return;
   }
-  for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (idx / ns) == (idx % ns) ? 1.0 : 0.0;
+  const double ah = fabs(h);
+  const double x = fma(h, h, g * g);
+  const double r = nr_range(x) ? x * rsqrt_nr(x) : sqrt(x);
+  const double q = 2.0 * r * (ah + r);
+  const double w = nr_range(q) ? rsqrt_nr(q) : 1.0 / sqrt(q);
+  c = (ah + r) * w;
+  sn = (h > 0.0 ? g : -g) * w;
+}
+
+__device__ __forceinline__ void jrot(float al, float be, float ga, float &c, float &sn) {
+  const float h = be - al, g = 2.0f * ga;
+  if (h == 0.0f) {
+    c = sn = 0.70710678f;
+    return;
+  }
+  const float ah = fabsf(h);
+  const float r = sqrtf(fmaf(h, h, g * g));
+  const float w = rsqrtf(2.0f * r * (ah + r));
+  c = (ah + r) * w;
+  sn = (h > 0.0f ? g : -g) * w;
+}
+
+// Round-robin one-sided Jacobi on A (ms x ns, column-major), accumulating the rotations
+// into V (ns x ns, column-major).  pos holds 2 * (ns + 2) ints, flag 1 int.  Returns
+// whether a sweep completed without rotating.  Pairs whose two columns both have squared
+// norms <= neg2 are left alone (deflation of negligible columns).
+template <typename T>
+__device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2) {
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
+  if (ns <= 1) return true;
   const int n2 = (ns + 1) & ~1;
+  const int stride = ns + 2;
   for (int i = t; i < n2; i += SVD_NT) pos[i] = i;
-  if (t == 0) flag[0] = 0;
   __syncthreads();
-  const double tol = 1e-15 * (double)ms;
-  int sweeps = 0, converged = 0;
   int cur = 0;
-  for (sweeps = 1; sweeps <= 60 && ns > 1; ++sweeps) {
+  const T tol2 = tol * tol;
+  for (int sweep = 0; sweep < maxsweeps; ++sweep) {
     if (t == 0) flag[0] = 0;
     __syncthreads();
     for (int round = 0; round < n2 - 1; ++round) {
-      int *P = pos + cur * (ns + 2);
+      const int *P = pos + cur * stride;
       for (int pr = warp; pr < n2 / 2; pr += nwarp) {
         int pp = P[pr], qq = P[n2 - 1 - pr];
         if (pp >= ns || qq >= ns) continue;
@@ -527,10 +557,10 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
           pp = qq;
           qq = tmp;
         }
-        double *bp = A + (size_t)pp * ms, *bq = A + (size_t)qq * ms;
-        double al = 0, be = 0, ga = 0;
+        T *bp = A + (size_t)pp * ms, *bq = A + (size_t)qq * ms;
+        T al = 0, be = 0, ga = 0;
         for (int r = lane; r < ms; r += 32) {
-          const double x = bp[r], y = bq[r];
+          const T x = bp[r], y = bq[r];
           al += x * x;
           be += y * y;
           ga += x * y;
@@ -538,39 +568,153 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
         al = warp_sum(al);
         be = warp_sum(be);
         ga = warp_sum(ga);
-        if (ga == 0.0 || fabs(ga) <= tol * sqrt(al) * sqrt(be)) continue;
-        const double zeta = (be - al) / (2.0 * ga);
-        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+        if (ga == T(0) || ga * ga <= tol2 * al * be || (al <= neg2 && be <= neg2)) continue;
+        T cs, sn;
+        jrot(al, be, ga, cs, sn);
         for (int r = lane; r < ms; r += 32) {
-          const double x = bp[r], y = bq[r];
+          const T x = bp[r], y = bq[r];
           bp[r] = cs * x - sn * y;
           bq[r] = sn * x + cs * y;
         }
-        double *vp = Vm + (size_t)pp * ns, *vq = Vm + (size_t)qq * ns;
+        T *vp = V + (size_t)pp * ns, *vq = V + (size_t)qq * ns;
         for (int r = lane; r < ns; r += 32) {
-          const double x = vp[r], y = vq[r];
+          const T x = vp[r], y = vq[r];
           vp[r] = cs * x - sn * y;
           vq[r] = sn * x + cs * y;
         }
         if (lane == 0) flag[0] = 1;
       }
       __syncthreads();
-      // tournament rotation: keep position 0, rotate the rest by one
-      int *Pn = pos + (cur ^ 1) * (ns + 2);
+      int *Pn = pos + (cur ^ 1) * stride;
       for (int i = t; i < n2; i += SVD_NT) Pn[i] = i == 0 ? P[0] : (i == 1 ? P[n2 - 1] : P[i - 1]);
       cur ^= 1;
       __syncthreads();
     }
     const int any = flag[0];
     __syncthreads();
-    if (!any) {
-      converged = 1;
-      break;
+    if (!any) return true;
+  }
+  return false;
+}
+
+// shared-memory doubles of the SVD kernel: A, V, work area W, sigma
+__host__ __device__ inline size_t svd_w_doubles(int ms, int ns) {
+  const size_t a = (size_t)ms * ns, b = 2 * (size_t)ns * ns;
+  return a > b ? a : b;
+}
+
+__global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int K = a.K, t = threadIdx.x;
+  const int Lc = *a.Lcur;
+  const int kroot = (int)min64((int64_t)Lc * a.In, K);
+  const bool wide = kroot < K;
+  const int ms = K, ns = wide ? kroot : K;  // A is ms x ns, column-major, ms >= ns
+  double *A = reinterpret_cast<double *>(smem);
+  double *Vm = A + (size_t)ms * ns;
+  double *W = Vm + (size_t)ns * ns;
+  const bool pre = a.precond != 0;
+  double *sig = pre ? W + svd_w_doubles(ms, ns) : W;
+  int *pos = reinterpret_cast<int *>(sig + ns);  // 2 * (ns + 2)
+  int *ord = pos + 2 * (ns + 2);
+  int *flag = ord + ns + 1;                      // 4
+  double *red = reinterpret_cast<double *>(flag + 4);  // SVD_NT / 32, 8-aligned below
+  red = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+  for (int idx = t; idx < ms * ns; idx += SVD_NT) {
+    const int c = idx / ms, r = idx - c * ms;
+    A[idx] = wide ? a.Rroot[(size_t)c * K + r] : a.Rroot[(size_t)r * K + c];
+  }
+  for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (idx / ns) == (idx % ns) ? 1.0 : 0.0;
+  __syncthreads();
+  if (pre && ns > 1) {
+    // scale by a power of two so the FP32 copy neither over- nor underflows
+    double amax = 0.0;
+    for (int idx = t; idx < ms * ns; idx += SVD_NT) amax = fmax(amax, fabs(A[idx]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((t & 31) == 0) red[t >> 5] = amax;
+    __syncthreads();
+    if (t == 0) {
+      double m = 0.0;
+      for (int w = 0; w < SVD_NT / 32; ++w) m = fmax(m, red[w]);
+      red[0] = m;
+    }
+    __syncthreads();
+    amax = red[0];
+    __syncthreads();
+    if (amax > 0.0 && amax < 1e300) {
+      const int ex = (int)((__double_as_longlong(amax) >> 52) & 0x7ff) - 1023;
+      const double scl = __longlong_as_double((long long)(1023 - ex) << 52);  // 2^-ex
+      float *A32 = reinterpret_cast<float *>(W);
+      float *V32 = A32 + (size_t)ms * ns;
+      for (int idx = t; idx < ms * ns; idx += SVD_NT) A32[idx] = (float)(A[idx] * scl);
+      for (int idx = t; idx < ns * ns; idx += SVD_NT) V32[idx] = (idx / ns) == (idx % ns) ? 1.0f : 0.0f;
+      __syncthreads();
+      // columns below FP32 resolution relative to the largest entry carry no information here
+      jacobi<float>(A32, V32, ms, ns, pos, flag, 4e-6f, 20, 1e-12f * (float)ms);
+      for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (double)V32[idx];
+      __syncthreads();
+      // Newton-Schulz: X = V^T V, V <- 1.5 V - 0.5 V X (twice); X and the new V in W
+      double *X = W, *Y = W + (size_t)ns * ns;
+      for (int it = 0; it < 2; ++it) {
+        for (int idx = t; idx < ns * ns; idx += SVD_NT) {
+          const int j = idx / ns, i = idx - j * ns;
+          double acc = 0.0;
+          for (int r = 0; r < ns; ++r) acc += Vm[(size_t)i * ns + r] * Vm[(size_t)j * ns + r];
+          X[idx] = acc;
+        }
+        __syncthreads();
+        for (int idx = t; idx < ns * ns; idx += SVD_NT) {
+          const int j = idx / ns, r = idx - j * ns;
+          double acc = 0.0;
+          for (int i = 0; i < ns; ++i) acc += Vm[(size_t)i * ns + r] * X[(size_t)j * ns + i];
+          Y[idx] = 1.5 * Vm[idx] - 0.5 * acc;
+        }
+        __syncthreads();
+        for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = Y[idx];
+        __syncthreads();
+      }
+      // B = A V (into W, then back into A)
+      for (int idx = t; idx < ms * ns; idx += SVD_NT) {
+        const int j = idx / ms, r = idx - j * ms;
+        double acc = 0.0;
+        for (int i = 0; i < ns; ++i) acc += A[(size_t)i * ms + r] * Vm[(size_t)j * ns + i];
+        W[idx] = acc;
+      }
+      __syncthreads();
+      for (int idx = t; idx < ms * ns; idx += SVD_NT) A[idx] = W[idx];
+      __syncthreads();
     }
   }
-  if (ns <= 1) converged = 1;
+  // Deflation threshold: columns whose squared norm is <= 1e-6 delta^2 / ns can never be
+  // kept by the rank rule and their total mass stays exact in the tails (sum of squared
+  // column norms), so pairs of two such columns need no rotation.  For n = 0, delta is
+  // taken from ||A||_F (= ||X||, Sec. 2.3) only to set this threshold.
+  {
+    double f2 = 0.0;
+    if (a.n == 0)
+      for (int idx = t; idx < ms * ns; idx += SVD_NT) f2 += A[idx] * A[idx];
+    f2 = warp_sum(f2);
+    if ((t & 31) == 0) red[t >> 5] = f2;
+    __syncthreads();
+    if (t == 0) {
+      double d2;
+      if (a.n == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < SVD_NT / 32; ++w) tot += red[w];
+        d2 = a.N > 1 ? a.eps * a.eps * tot / (double)(a.N - 1) : 0.0;
+      } else {
+        d2 = a.scal[1] * a.scal[1];
+      }
+      sig[0] = 1e-6 * d2 / (double)ns;
+    }
+    __syncthreads();
+  }
+  const double neg2 = sig[0];
+  __syncthreads();
+  const bool converged = jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2);
   // singular values
+  const int lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   for (int c = warp; c < ns; c += nwarp) {
     double ss = 0;
     for (int r = lane; r < ms; r += 32) ss += A[(size_t)c * ms + r] * A[(size_t)c * ms + r];
@@ -617,7 +761,6 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   }
   __syncthreads();
   const int L = flag[1];
-  // outputs
   for (int idx = t; idx < K * L; idx += SVD_NT) {
     const int r = idx / L, l = idx - r * L;
     const int c = ord[l];
@@ -850,8 +993,10 @@ SmemTree smem_tree(int b, int cmax) {
   return m;
 }
 
-size_t smem_svd(int K) {
-  return sizeof(double) * ((size_t)K * K * 2 + K) + sizeof(int) * (3 * (size_t)K + 16);
+// shared bytes of k_svd for K columns (ms = ns = K is the largest case)
+size_t smem_svd(int K, bool precond) {
+  const size_t w = precond ? svd_w_doubles(K, K) : 0;
+  return sizeof(double) * ((size_t)K * K * 2 + w + K + SVD_NT / 32 + 1) + sizeof(int) * (3 * (size_t)K + 16);
 }
 
 struct CorePlan {
@@ -970,7 +1115,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl) {
   if (N > 1 && !choose_tiles<T>(pl)) return TT_ERR_UNSUPPORTED;
   // svd and tree shared-memory limits
   for (int n = 0; n + 1 < N; ++n)
-    if (smem_svd(pl.core[n].K1) > kSmemBudget) return TT_ERR_UNSUPPORTED;
+    if (smem_svd(pl.core[n].K1, false) > kSmemBudget) return TT_ERR_UNSUPPORTED;
   // workspace layout
   Carve w;
   pl.off_L = w.take(sizeof(int) * (N + 1), 256);
@@ -1267,7 +1412,8 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.Cnext = C1 + cn.tree.node_off[cn.tree.nlev] * (size_t)B * B;
       a.ldu = B;
       a.status = dstatus;
-      const size_t bytes = smem_svd(K1);
+      a.precond = smem_svd(K1, true) <= kSmemBudget;
+      const size_t bytes = smem_svd(K1, a.precond != 0);
       r = set_smem(k_svd, bytes);
       if (r) return r;
       {
