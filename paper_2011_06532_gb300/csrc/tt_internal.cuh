@@ -159,24 +159,22 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
         if (ss != T(0)) {
           const T alpha = piv[j];
           const T v = alpha * alpha + ss;
-          T nrm, q;
-          // one reciprocal: with d = alpha - beta and q = 1 / (beta d),
-          // tau = (beta - alpha) / beta = -d d q and 1 / d = beta q
-          if (sizeof(T) == 8 && nr_range((double)v)) {
-            nrm = (T)((double)v * rsqrt_nr((double)v));
-          } else {
-            nrm = tsqrt(v);
-          }
+          const bool fast = sizeof(T) == 8 && nr_range((double)v);
+          const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
           const T beta = alpha >= T(0) ? -nrm : nrm;
           const T d = alpha - beta;
           const T bd = beta * d;
-          if (sizeof(T) == 8 && nr_range(fabs((double)bd))) {
-            q = (T)rcp_nr((double)bd);
+          if (fast && nr_range(fabs((double)bd))) {
+            // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q
+            // and 1 / d = beta q
+            const T q = (T)rcp_nr((double)bd);
+            tj = -d * d * q;
+            scale = beta * q;
           } else {
-            q = T(1) / bd;
+            // textbook form; tau lies in [1, 2] whatever the scale of the column
+            tj = (beta - alpha) / beta;
+            scale = T(1) / d;
           }
-          tj = -d * d * q;
-          scale = beta * q;
           piv[j] = beta;
         }
         tau[j] = tj;

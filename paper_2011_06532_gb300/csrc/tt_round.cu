@@ -526,6 +526,11 @@ __device__ __forceinline__ void jrot(float al, float be, float ga, float &c, flo
   const float ah = fabsf(h);
   const float r = sqrtf(fmaf(h, h, g * g));
   const float w = rsqrtf(2.0f * r * (ah + r));
+  if (!(w < 3.0e38f)) {  // underflowed operands: leave the pair alone
+    c = 1.0f;
+    sn = 0.0f;
+    return;
+  }
   c = (ah + r) * w;
   sn = (h > 0.0f ? g : -g) * w;
 }
@@ -652,7 +657,18 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
       __syncthreads();
       // columns below FP32 resolution relative to the largest entry carry no information here
       jacobi<float>(A32, V32, ms, ns, pos, flag, 4e-6f, 20, 1e-12f * (float)ms);
-      for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (double)V32[idx];
+      int *bad = flag + 2;
+      if (t == 0) *bad = 0;
+      __syncthreads();
+      for (int idx = t; idx < ns * ns; idx += SVD_NT) {
+        const double v = (double)V32[idx];
+        if (!isfinite(v)) *bad = 1;
+        Vm[idx] = v;
+      }
+      __syncthreads();
+      if (*bad) {  // no usable preconditioner: start the FP64 sweeps from V = I
+        for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (idx / ns) == (idx % ns) ? 1.0 : 0.0;
+      }
       __syncthreads();
       // Newton-Schulz: X = V^T V, V <- 1.5 V - 0.5 V X (twice); X and the new V in W
       double *X = W, *Y = W + (size_t)ns * ns;
@@ -1032,10 +1048,24 @@ static int device_sm_count() {
 }
 
 template <typename T>
-static bool choose_tiles(RoundPlan &pl) {
+static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
   const int N = pl.N;
   for (int n = 0; n < N; ++n) {
     CorePlan &c = pl.core[n];
+    if (sweep1_only) {
+      // the orthonormalization norm runs the right-to-left sweep only
+      if (n == 0) continue;
+      int best1 = 0;
+      for (int Tt = 1; Tt <= 64 && Tt <= (c.I + c.P - 1) / c.P; ++Tt) {
+        if (Tt * c.K1 > 512 && Tt > 1) break;
+        if (smem_s1<T>(c.R0, c.K1, c.R1, Tt, 8).bytes > kSmemBudget) break;
+        best1 = Tt;
+        if (smem_s1<T>(c.R0, c.K1, c.R1, Tt, 8).bytes > kSmemPair && best1 > 1) break;
+      }
+      if (best1 == 0) return false;
+      c.Tt = best1;
+      continue;
+    }
     const int64_t per_leaf = (c.I + c.P - 1) / c.P;
     int best = 0;
     const int CC = 8;
@@ -1085,7 +1115,7 @@ static bool choose_tiles(RoundPlan &pl) {
 }
 
 template <typename T>
-static int make_plan(const tt_tensor *x, RoundPlan &pl) {
+static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false) {
   const int N = x->N;
   pl.N = N;
   pl.dtype = x->dtype;
@@ -1112,10 +1142,12 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl) {
     c.P = leaves_for(c.I, pl.nsm);
     c.tree = make_tree(c.P);
   }
-  if (N > 1 && !choose_tiles<T>(pl)) return TT_ERR_UNSUPPORTED;
+  if (N > 1 && !choose_tiles<T>(pl, sweep1_only)) return TT_ERR_UNSUPPORTED;
   // svd and tree shared-memory limits
-  for (int n = 0; n + 1 < N; ++n)
+  for (int n = 0; n + 1 < N && !sweep1_only; ++n)
     if (smem_svd(pl.core[n].K1, false) > kSmemBudget) return TT_ERR_UNSUPPORTED;
+  for (int n = 1; n < N; ++n)
+    if (smem_tree(pl.core[n].R0, 1).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
   // workspace layout
   Carve w;
   pl.off_L = w.take(sizeof(int) * (N + 1), 256);
@@ -1520,7 +1552,13 @@ int round_run(const tt_tensor *x, double eps, tt_tensor *out, void *ws, size_t w
   return x->dtype == TT_F64 ? run_round<double>(pl, x, eps, out, w, st) : run_round<float>(pl, x, eps, out, w, st);
 }
 
-int norm_workspace(const tt_tensor *x, size_t *bytes) { return round_workspace(x, bytes); }
+int norm_workspace(const tt_tensor *x, size_t *bytes) {
+  RoundPlan pl;
+  int st = x->dtype == TT_F64 ? make_plan<double>(x, pl, true) : make_plan<float>(x, pl, true);
+  if (st) return st;
+  *bytes = pl.total;
+  return TT_OK;
+}
 
 template <typename T>
 static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, unsigned char *ws, cudaStream_t st) {
@@ -1552,7 +1590,7 @@ static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, uns
 
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st) {
   RoundPlan pl;
-  int r = x->dtype == TT_F64 ? make_plan<double>(x, pl) : make_plan<float>(x, pl);
+  int r = x->dtype == TT_F64 ? make_plan<double>(x, pl, true) : make_plan<float>(x, pl, true);
   if (r) return r;
   if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
   unsigned char *w = reinterpret_cast<unsigned char *>(ws);
