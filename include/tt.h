@@ -17,10 +17,13 @@
  * Sec. 2.2 are both column-major.  Core buffers live in device memory of the
  * current CUDA device.
  *
- * Element type.  dtype TT_F64: every step computes in FP64.  dtype TT_F32:
- * core streams and the per-slab Householder work run in FP32 while the small
- * factors (triangular-factor reduction trees, SVDs, rank choice, norm) stay in
- * FP64; the result is stored in FP32.
+ * Element type and precision.  dtype TT_F64 (TT_PREC_FP64): every step
+ * computes in FP64.  dtype TT_F32: cores are stored and streamed in FP32; the
+ * per-slab work (push, Householder QR and its applications) runs on the FP32
+ * pipes either in double-float arithmetic (TT_PREC_FP32X2: each value an
+ * unevaluated sum of two FP32 numbers, about 2^-46 relative accuracy) or in
+ * plain FP32 (TT_PREC_FP32); the small factors (triangular-factor reduction
+ * trees, SVDs, rank choice, norm) stay in FP64; the result is stored in FP32.
  *
  * Ownership.  The library never allocates memory.  Inputs are borrowed and
  * never modified.  Outputs are caller-owned device buffers.  Routines that need
@@ -57,6 +60,13 @@ typedef enum {
 
 typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
 
+typedef enum {
+  TT_PREC_DEFAULT = 0, /* TT_PREC_FP64 for TT_F64 cores, TT_PREC_FP32X2 for TT_F32 cores */
+  TT_PREC_FP64 = 1,    /* TT_F64 cores only */
+  TT_PREC_FP32X2 = 2,  /* TT_F32 cores: double-float slab arithmetic, FP64 small factors */
+  TT_PREC_FP32 = 3     /* TT_F32 cores: FP32 slab arithmetic, FP64 small factors */
+} tt_precision;
+
 /* Largest rank (R[n]) any routine accepts. */
 #define TT_MAX_RANK 128
 
@@ -71,9 +81,10 @@ typedef struct {
 } tt_tensor;
 
 /*
- * Workspace bytes tt_round needs for input x (depends on N, I, R, dtype only).
+ * Workspace bytes tt_round needs for input x at `precision` (a tt_precision;
+ * depends on N, I, R, dtype and precision only).
  */
-int tt_round_workspace_size(const tt_tensor *x, size_t *bytes);
+int tt_round_workspace_size(const tt_tensor *x, int precision, size_t *bytes);
 
 /*
  * TT rounding (Alg. 2, organised as Alg. 6): a right-to-left sweep takes a
@@ -86,6 +97,7 @@ int tt_round_workspace_size(const tt_tensor *x, size_t *bytes);
  *
  * x      input tensor (read only).
  * eps    relative accuracy, finite and >= 0.
+ * precision  a tt_precision matching x->dtype (TT_PREC_DEFAULT picks it).
  * out    out->N, out->dtype and out->I must match x; out->cores[n] must hold at
  *        least x->R[n] * I[n] * x->R[n+1] elements (ranks never grow).  On
  *        return out->R holds the new ranks and core n holds
@@ -95,15 +107,16 @@ int tt_round_workspace_size(const tt_tensor *x, size_t *bytes);
  * N = 1 copies the single core.  A zero tensor returns ranks all 1 and zero
  * cores.  Synchronizes `stream` before returning.
  */
-int tt_round(const tt_tensor *x, double eps, tt_tensor *out, void *workspace, size_t workspace_bytes, void *stream);
+int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void *workspace, size_t workspace_bytes,
+             void *stream);
 
 /*
  * Rounds `count` independent tensors with one shared workspace, queueing them
  * back to back on `stream` (each entry as in tt_round; eps[k] per tensor).
  * workspace_bytes must cover the largest tt_round_workspace_size of the batch.
  */
-int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, tt_tensor *outs, void *workspace,
-                     size_t workspace_bytes, void *stream);
+int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                     void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Summation (Sec. 3.2.1): Z = A + B.  Interior slices are block diagonal

@@ -25,6 +25,8 @@ __all__ = ["DeviceTT", "build", "tt_round", "tt_round_batched", "tt_add", "tt_ha
            "TTError", "from_host", "to_host", "trace", "trace_read"]
 
 _DTYPES = {torch.float64: 0, torch.float32: 1}
+# tt_precision: "default" (fp64 for float64 cores, fp32x2 for float32), "fp64", "fp32x2", "fp32"
+PRECISIONS = {"default": 0, "fp64": 1, "fp32x2": 2, "fp32": 3}
 
 
 class TTError(RuntimeError):
@@ -105,35 +107,39 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
     return buf
 
 
-def round_workspace_size(x: DeviceTT) -> int:
+def round_workspace_size(x: DeviceTT, precision: str = "default") -> int:
     lib = _native.load()
     d = _Desc(x.I, x.R, x.cores, x.dtype)
     n = ctypes.c_size_t(0)
-    _check(lib.tt_round_workspace_size(d.ref, ctypes.byref(n)), "tt_round_workspace_size")
+    _check(lib.tt_round_workspace_size(d.ref, PRECISIONS[precision], ctypes.byref(n)), "tt_round_workspace_size")
     return int(n.value)
 
 
 def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tensor]] = None,
-             workspace: Optional[torch.Tensor] = None) -> DeviceTT:
-    """TT rounding (Alg. 2 / Alg. 6): returns Y with ||X - Y|| <= eps ||X||."""
+             workspace: Optional[torch.Tensor] = None, precision: str = "default") -> DeviceTT:
+    """TT rounding (Alg. 2 / Alg. 6): returns Y with ||X - Y|| <= eps ||X||.
+
+    precision: "default", "fp64" (float64 cores), "fp32x2" or "fp32" (float32 cores)."""
     _validate(x)
     lib = _native.load()
     dev = x.cores[0].device
+    prec = PRECISIONS[precision]
     d = _Desc(x.I, x.R, x.cores, x.dtype)
     n = ctypes.c_size_t(0)
-    _check(lib.tt_round_workspace_size(d.ref, ctypes.byref(n)), "tt_round_workspace_size")
+    _check(lib.tt_round_workspace_size(d.ref, prec, ctypes.byref(n)), "tt_round_workspace_size")
     ws = workspace if workspace is not None else _workspace(int(n.value), dev)
     if out is None:
         out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
     o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
-    _check(lib.tt_round(d.ref, float(eps), o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+    _check(lib.tt_round(d.ref, float(eps), prec, o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
                         _stream(stream)), "tt_round")
     R = o.ranks()
     cores = [out[k][: R[k] * x.I[k] * R[k + 1]] for k in range(x.N)]
     return DeviceTT(list(x.I), R, cores)
 
 
-def tt_round_batched(xs: Sequence[DeviceTT], eps: Sequence[float], stream=None) -> List[DeviceTT]:
+def tt_round_batched(xs: Sequence[DeviceTT], eps: Sequence[float], stream=None,
+                     precision: str = "default") -> List[DeviceTT]:
     """Rounds several independent tensors with one call (shared workspace)."""
     lib = _native.load()
     if not xs:
@@ -142,14 +148,14 @@ def tt_round_batched(xs: Sequence[DeviceTT], eps: Sequence[float], stream=None) 
         _validate(x)
     dev = xs[0].cores[0].device
     descs = [_Desc(x.I, x.R, x.cores, x.dtype) for x in xs]
-    need = max(round_workspace_size(x) for x in xs)
+    need = max(round_workspace_size(x, precision) for x in xs)
     ws = _workspace(need, dev)
     outs = [[torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()] for x in xs]
     odescs = [_Desc(x.I, [1] * (x.N + 1), o, x.dtype) for x, o in zip(xs, outs)]
     arr_in = (_native.TTTensor * len(xs))(*[d.s for d in descs])
     arr_out = (_native.TTTensor * len(xs))(*[d.s for d in odescs])
     e = (ctypes.c_double * len(xs))(*[float(v) for v in eps])
-    _check(lib.tt_round_batched(len(xs), arr_in, e, arr_out, ctypes.c_void_p(ws.data_ptr()),
+    _check(lib.tt_round_batched(len(xs), arr_in, e, PRECISIONS[precision], arr_out, ctypes.c_void_p(ws.data_ptr()),
                                 ctypes.c_size_t(ws.numel()), _stream(stream)), "tt_round_batched")
     res = []
     for k, x in enumerate(xs):

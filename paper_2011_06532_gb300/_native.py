@@ -95,9 +95,9 @@ def load(path: str | None = None):
     vp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)
     dp = ctypes.POINTER(ctypes.c_double)
     sigs = {
-        "tt_round_workspace_size": [T, sz],
-        "tt_round": [T, ctypes.c_double, T, vp, ctypes.c_size_t, vp],
-        "tt_round_batched": [ctypes.c_int32, T, dp, T, vp, ctypes.c_size_t, vp],
+        "tt_round_workspace_size": [T, ctypes.c_int, sz],
+        "tt_round": [T, ctypes.c_double, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_round_batched": [ctypes.c_int32, T, dp, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
         "tt_add": [T, T, T, vp],
         "tt_hadamard": [T, T, T, vp],
         "tt_dot_workspace_size": [T, T, sz],

@@ -45,6 +45,14 @@ bool same_modes(const tt_tensor *a, const tt_tensor *b) {
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// resolves TT_PREC_DEFAULT and checks that the precision fits the element type; -1 if not
+int resolve_prec(const tt_tensor *x, int prec) {
+  if (prec == TT_PREC_DEFAULT) return x->dtype == TT_F64 ? TT_PREC_FP64 : TT_PREC_FP32X2;
+  if (prec == TT_PREC_FP64) return x->dtype == TT_F64 ? prec : -1;
+  if (prec == TT_PREC_FP32X2 || prec == TT_PREC_FP32) return x->dtype == TT_F32 ? prec : -1;
+  return -1;
+}
+
 }  // namespace
 
 namespace ttgb {
@@ -121,32 +129,39 @@ int tt_trace_read(int kind, int64_t *launches, double *milliseconds) {
   return TT_OK;
 }
 
-int tt_round_workspace_size(const tt_tensor *x, size_t *bytes) {
+int tt_round_workspace_size(const tt_tensor *x, int precision, size_t *bytes) {
   if (!valid_tensor(x) || !bytes) return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
   if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
   if (x->N == 1) {
     *bytes = 0;
     return TT_OK;
   }
-  return ttgb::round_workspace(x, bytes);
+  return ttgb::round_workspace(x, prec, bytes);
 }
 
-int tt_round(const tt_tensor *x, double eps, tt_tensor *out, void *workspace, size_t workspace_bytes, void *stream) {
+int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void *workspace, size_t workspace_bytes,
+             void *stream) {
   if (!valid_tensor(x) || !valid_out(x, out) || !(eps >= 0.0) || !isfinite(eps)) return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
   if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
-  return ttgb::round_run(x, eps, out, workspace, workspace_bytes, as_stream(stream));
+  return ttgb::round_run(x, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
 }
 
-int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, tt_tensor *outs, void *workspace,
-                     size_t workspace_bytes, void *stream) {
+int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                     void *workspace, size_t workspace_bytes, void *stream) {
   if (count < 0 || (count > 0 && (!xs || !eps || !outs))) return TT_ERR_INVALID_ARG;
   for (int k = 0; k < count; ++k) {
     if (!valid_tensor(&xs[k]) || !valid_out(&xs[k], &outs[k]) || !(eps[k] >= 0.0) || !isfinite(eps[k]))
       return TT_ERR_INVALID_ARG;
+    if (resolve_prec(&xs[k], precision) < 0) return TT_ERR_INVALID_ARG;
     if (!ranks_supported(&xs[k])) return TT_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < count; ++k) {
-    const int st = ttgb::round_run(&xs[k], eps[k], &outs[k], workspace, workspace_bytes, as_stream(stream));
+    const int st = ttgb::round_run(&xs[k], eps[k], resolve_prec(&xs[k], precision), &outs[k], workspace,
+                                   workspace_bytes, as_stream(stream));
     if (st) return st;
   }
   return TT_OK;

@@ -16,9 +16,129 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace ttgb {
 
 constexpr int NT = 256;  // threads per CTA of every bulk kernel
+
+// ------------------------------------------------------------------------------------
+// df32: a value stored as an unevaluated sum hi + lo of two FP32 numbers ("double-word"
+// or double-single arithmetic).  Built from the error-free transformations TwoSum
+// (Knuth), FastTwoSum (Dekker) and the FMA-based exact product, in the forms analysed by
+// Joldes, Muller, Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic" (ACM TOMS 2017): addition (their accurate DW+DW), multiplication
+// (DW x DW with FMA), division and square root by one correction step.  Relative accuracy
+// about 2^-46, computed entirely on the FP32 pipes (58x the FP64 rate on GB300).
+// ------------------------------------------------------------------------------------
+
+struct df32 {
+  float hi, lo;
+  __host__ __device__ df32() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr df32(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ df32(float x) : hi(x), lo(0.f) {}
+  __host__ __device__ df32(int x) : hi((float)x), lo(0.f) {}
+  __device__ explicit df32(double x) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+  }
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ df32 operator+(df32 x, df32 y) {
+  float s, e, t, f;
+  two_sum(x.hi, y.hi, s, e);
+  two_sum(x.lo, y.lo, t, f);
+  e += t;
+  fast_two_sum(s, e, s, e);
+  e += f;
+  fast_two_sum(s, e, s, e);
+  return df32(s, e);
+}
+__device__ __forceinline__ df32 operator-(df32 x) { return df32(-x.hi, -x.lo); }
+__device__ __forceinline__ df32 operator-(df32 x, df32 y) { return x + (-y); }
+__device__ __forceinline__ df32 operator*(df32 x, df32 y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  float s;
+  fast_two_sum(p, e, s, e);
+  return df32(s, e);
+}
+__device__ __forceinline__ df32 operator/(df32 x, df32 y) {
+  const float q = x.hi / y.hi;
+  const df32 r = x - df32(q) * y;  // remainder, nearly exact
+  const float q2 = r.hi / y.hi;
+  float s, e;
+  fast_two_sum(q, q2, s, e);
+  return df32(s, e);
+}
+__device__ __forceinline__ df32 &operator+=(df32 &x, df32 y) { return x = x + y; }
+__device__ __forceinline__ df32 &operator-=(df32 &x, df32 y) { return x = x - y; }
+__device__ __forceinline__ df32 &operator*=(df32 &x, df32 y) { return x = x * y; }
+__device__ __forceinline__ bool operator==(df32 x, df32 y) { return x.hi == y.hi && x.lo == y.lo; }
+__device__ __forceinline__ bool operator!=(df32 x, df32 y) { return !(x == y); }
+__device__ __forceinline__ bool operator>=(df32 x, df32 y) {
+  return x.hi > y.hi || (x.hi == y.hi && x.lo >= y.lo);
+}
+__device__ __forceinline__ df32 df_sqrt(df32 x) {
+  if (x.hi <= 0.f) return df32(0.f);
+  const float sq = sqrtf(x.hi);
+  // x - sq^2 with the exact product sq * sq
+  const float p = sq * sq;
+  const float pe = fmaf(sq, sq, -p);
+  const df32 r = x - df32(p, pe);
+  const float c = r.hi / (2.f * sq);
+  float s, e;
+  fast_two_sum(sq, c, s, e);
+  return df32(s, e);
+}
+
+// accumulate a + b * c into an unevaluated (s, comp) pair: the compensated dot product
+// of Ogita, Rump, Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005,
+// Dot2) extended to double-word operands; finish with df_finish(s, comp).
+__device__ __forceinline__ void df_dot_acc(float &s, float &comp, df32 b, df32 c) {
+  const float p = b.hi * c.hi;
+  float e = fmaf(b.hi, c.hi, -p);
+  e = fmaf(b.hi, c.lo, e);
+  e = fmaf(b.lo, c.hi, e);
+  float t;
+  two_sum(s, p, s, t);
+  comp += t + e;
+}
+__device__ __forceinline__ df32 df_finish(float s, float comp) {
+  float h, l;
+  fast_two_sum(s, comp, h, l);
+  return df32(h, l);
+}
+// x - v * w with one normalisation
+__device__ __forceinline__ df32 df_sub_prod(df32 x, df32 v, df32 w) {
+  const float p = v.hi * w.hi;
+  float e = fmaf(v.hi, w.hi, -p);
+  e = fmaf(v.hi, w.lo, e);
+  e = fmaf(v.lo, w.hi, e);
+  float s, t;
+  two_sum(x.hi, -p, s, t);
+  t += x.lo - e;
+  fast_two_sum(s, t, s, t);
+  return df32(s, t);
+}
+
+template <typename T>
+struct is_df : std::false_type {};
+template <>
+struct is_df<df32> : std::true_type {};
 
 template <typename T>
 __device__ __forceinline__ T tsqrt(T x);
@@ -26,6 +146,8 @@ template <>
 __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ df32 tsqrt<df32>(df32 x) { return df_sqrt(x); }
 
 // FP64 reciprocal and reciprocal square root by Newton-Raphson iteration from a
 // single-precision hardware seed.  On GB300 every FP64 instruction occupies an SMSP's
@@ -69,6 +191,15 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+template <>
+__device__ __forceinline__ df32 warp_sum<df32>(df32 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const df32 u(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    v = v + u;
+  }
+  return v;
+}
 
 // Scratch a block-level routine needs in shared memory.
 template <typename T>
@@ -91,9 +222,15 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
   // partial dot products v^T X(:, c) over row groups
   if (t < G * nc) {
     const int g = t / nc, c = t - g * nc;
-    T acc = T(0);
-    for (int r = r0 + g; r < M; r += G) acc += V[(size_t)r * ldv] * X[(size_t)r * ldx + c];
-    s.red[g * nc + c] = acc;
+    if constexpr (is_df<T>::value) {
+      float sh = 0.f, sc = 0.f;
+      for (int r = r0 + g; r < M; r += G) df_dot_acc(sh, sc, V[(size_t)r * ldv], X[(size_t)r * ldx + c]);
+      s.red[g * nc + c] = df_finish(sh, sc);
+    } else {
+      T acc = T(0);
+      for (int r = r0 + g; r < M; r += G) acc += V[(size_t)r * ldv] * X[(size_t)r * ldx + c];
+      s.red[g * nc + c] = acc;
+    }
   }
   __syncthreads();
   for (int h = G; h > 1;) {
@@ -113,7 +250,12 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
     const int dq = NT / nc, dr = NT - dq * nc;
     int r = t / nc, c = t - (t / nc) * nc;
     for (; r < nrow;) {
-      X[(size_t)(r0 + r) * ldx + c] -= V[(size_t)(r0 + r) * ldv] * s.wbuf[c];
+      if constexpr (is_df<T>::value) {
+        T &x = X[(size_t)(r0 + r) * ldx + c];
+        x = df_sub_prod(x, V[(size_t)(r0 + r) * ldv], s.wbuf[c]);
+      } else {
+        X[(size_t)(r0 + r) * ldx + c] -= V[(size_t)(r0 + r) * ldv] * s.wbuf[c];
+      }
       r += dq;
       c += dr;
       if (c >= nc) {
@@ -159,7 +301,7 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
         if (ss != T(0)) {
           const T alpha = piv[j];
           const T v = alpha * alpha + ss;
-          const bool fast = sizeof(T) == 8 && nr_range((double)v);
+          const bool fast = std::is_same<T, double>::value && nr_range((double)v);
           const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
           const T beta = alpha >= T(0) ? -nrm : nrm;
           const T d = alpha - beta;

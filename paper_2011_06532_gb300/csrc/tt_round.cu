@@ -38,9 +38,9 @@ struct Geom {
   int Tt;     // slices per tile
 };
 
-template <typename T>
+template <typename S, typename T>
 struct S1Args {
-  const T *X;  // core n: b x I x cin
+  const S *X;  // core n: b x I x cin
   Geom g;
   int b, cin, rho;   // columns (R_n), right rank of X (R_{n+1}), rows per slice (K_{n+1})
   const double *Pm;  // rho x cin row-major (upper trapezoidal), nullptr = identity (rho == cin == 1)
@@ -72,7 +72,7 @@ struct TreeArgs {
   int lda;
 };
 
-template <typename T>
+template <typename S, typename T>
 struct S2Args {
   // mode A (core n >= 1): apply stored sweep-1 Q_n to C; mode B (core 0): push X_0
   int mode;       // 0 = A, 1 = B, 2 = last core (mode A, write output, no V-QR)
@@ -86,7 +86,7 @@ struct S2Args {
   int ldc;
   const int *Lcur;      // &L[n]: columns of C = rows per slice of V(Y_n)
   // mode B
-  const T *X0;          // core 0: 1 x I x cin
+  const S *X0;          // core 0: 1 x I x cin
   int cin;
   const double *Pm;     // K1 x cin
   int CC;
@@ -94,12 +94,12 @@ struct S2Args {
   T *vrefl;             // (I*L) x K1 (V-QR reflectors)
   T *vtau;              // I x K1
   double *Rleaf;        // P x K1*K1
-  T *out;               // last core output (L x I x 1)
+  S *out;               // last core output (L x I x 1)
   int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv;
   int ldq, ldv;
 };
 
-template <typename T>
+template <typename S, typename T>
 struct OutArgs {
   Geom g;
   const T *vrefl;
@@ -109,7 +109,7 @@ struct OutArgs {
   const int *Lnext;     // &L[n+1]
   const double *Uleaf;  // per leaf: U (k'_leaf x Lnext), leading dim ldc
   int ldc;
-  T *out;               // output core n: L[n] x I x L[n+1]
+  S *out;               // output core n: L[n] x I x L[n+1]
   int oV, oCT, oCR, oRed, oW, oSc, oTau;
   int ldv;
 };
@@ -150,8 +150,8 @@ __device__ __forceinline__ int64_t rows_of_leaves(int64_t I, int P, int l0, int 
 // sweep 1 leaf: push + sequential Householder over tiles
 // ------------------------------------------------------------------------------------
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<T> a) {
+template <typename S, typename T>
+__global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *Rr = sm<T>(smem, a.oRr), *tile = sm<T>(smem, a.oTile), *Xs = sm<T>(smem, a.oXs), *Ps = sm<T>(smem, a.oPs);
   Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
@@ -160,7 +160,10 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<T> a) {
   const int b = a.b, rho = a.rho, cin = a.cin, ldt = a.ldt;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
   const bool push = a.Pm != nullptr;
-  if (push)
+  // FP64 reads the pushed factor straight from L1/L2 (no conversion, no shared copy);
+  // other compute types stage a converted copy
+  constexpr bool stage = !std::is_same<T, double>::value;
+  if (push && stage)
     for (int idx = t; idx < rho * cin; idx += NT) Ps[idx] = (T)a.Pm[idx];
   for (int idx = t; idx < b * b; idx += NT) Rr[idx] = T(0);
   __syncthreads();
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<T> a) {
       // rho == cin == 1: the tile rows are the slices themselves
       for (int idx = t; idx < M * b; idx += NT) {
         const int r = idx / b, c = idx - r * b;
-        tile[r * ldt + c] = a.X[(size_t)(i0 + r) * b + c];
+        tile[r * ldt + c] = T(a.X[(size_t)(i0 + r) * b + c]);
       }
     } else {
       for (int idx = t; idx < M * b; idx += NT) {
@@ -185,7 +188,7 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<T> a) {
         const int chunk = nt * b;
         for (int idx = t; idx < cc_n * chunk; idx += NT) {
           const int cc = idx / chunk, rem = idx - cc * chunk;
-          Xs[idx] = a.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem];
+          Xs[idx] = T(a.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem]);
         }
         __syncthreads();
         for (int idx = t; idx < M * b; idx += NT) {
@@ -193,20 +196,27 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<T> a) {
           const int sl = r / rho, kr = r - sl * rho;
           T acc = tile[r * ldt + col];
           const int cstart = max(kr, c0);
-          for (int c = cstart; c < c0 + cc_n; ++c) acc += Ps[kr * cin + c] * Xs[((c - c0) * nt + sl) * b + col];
+          if constexpr (stage) {
+            for (int c = cstart; c < c0 + cc_n; ++c) acc += Ps[kr * cin + c] * Xs[((c - c0) * nt + sl) * b + col];
+          } else {
+            const double *pr = a.Pm + (size_t)kr * cin;
+            for (int c = cstart; c < c0 + cc_n; ++c) acc += T(__ldg(pr + c)) * Xs[((c - c0) * nt + sl) * b + col];
+          }
           tile[r * ldt + col] = acc;
         }
       }
     }
     __syncthreads();
     const int kk = hh_factor(Rr, b, k, tile, ldt, M, b, taus, s);
-    // store reflectors and taus
-    T *dst = a.refl + (size_t)i0 * rho * b;
-    for (int idx = t; idx < M * b; idx += NT) {
-      const int r = idx / b, c = idx - r * b;
-      dst[idx] = tile[r * ldt + c];
+    // store reflectors and taus (the orthonormalization norm needs only R: refl == nullptr)
+    if (a.refl) {
+      T *dst = a.refl + (size_t)i0 * rho * b;
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int r = idx / b, c = idx - r * b;
+        dst[idx] = tile[r * ldt + c];
+      }
+      for (int j = t; j < kk; j += NT) a.tau[(size_t)i0 * b + j] = taus[j];
     }
-    for (int j = t; j < kk; j += NT) a.tau[(size_t)i0 * b + j] = taus[j];
     hh_take_rows(Rr, b, k, kk, tile, ldt, b);
     k = kk;
   }
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(NT) k_tree_factor(TreeArgs a) {
   for (int c = c0 + 1; c < c1; ++c) {
     const int kc = child_rows_k(a, c, rho);
     const double *Rc = a.Rin + (size_t)c * b * b;
-    double *slot = a.slots + (size_t)c * (b * b + a.nchunk * b);
+    double *slot = a.slots ? a.slots + (size_t)c * (b * b + a.nchunk * b) : nullptr;
     for (int ch = 0, ra = 0; ra < kc; ++ch, ra += a.MT) {
       const int M = min(a.MT, kc - ra);
       for (int idx = t; idx < M * b; idx += NT) {
@@ -248,11 +258,13 @@ __global__ void __launch_bounds__(NT) k_tree_factor(TreeArgs a) {
       }
       __syncthreads();
       const int kk = hh_factor(Rr, b, k, tile, a.lda, M, b, taus, s, ra);
-      for (int idx = t; idx < M * b; idx += NT) {
-        const int r = idx / b, col = idx - r * b;
-        slot[(size_t)(ra + r) * b + col] = tile[r * a.lda + col];
+      if (a.slots) {
+        for (int idx = t; idx < M * b; idx += NT) {
+          const int r = idx / b, col = idx - r * b;
+          slot[(size_t)(ra + r) * b + col] = tile[r * a.lda + col];
+        }
+        for (int j = t; j < b; j += NT) slot[(size_t)b * b + ch * b + j] = j < kk ? taus[j] : 0.0;
       }
-      for (int j = t; j < b; j += NT) slot[(size_t)b * b + ch * b + j] = j < kk ? taus[j] : 0.0;
       hh_take_rows(Rr, b, k, kk, tile, a.lda, b);
       k = kk;
     }
@@ -333,8 +345,8 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
 //               (last) apply Q_{N-1} and write the last output core
 // ------------------------------------------------------------------------------------
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<T> a) {
+template <typename S, typename T>
+__global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *Q = sm<T>(smem, a.oQ), *CT = sm<T>(smem, a.oCT), *CR = sm<T>(smem, a.oCR), *Rr = sm<T>(smem, a.oRr);
   T *Xs = sm<T>(smem, a.oXs), *Ps = sm<T>(smem, a.oPs);
@@ -388,7 +400,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<T> a) {
         // last core: Y[l, i, 0] = CT[(i - i0)][l]  (K1 == 1)
         for (int idx = t; idx < nt * L; idx += NT) {
           const int il = idx / L, l = idx - il * L;
-          a.out[(size_t)l + (size_t)L * (i0 + il)] = CT[il * L + l];
+          a.out[(size_t)l + (size_t)L * (i0 + il)] = (S)CT[il * L + l];
         }
         __syncthreads();
         continue;
@@ -408,7 +420,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<T> a) {
         __syncthreads();
         for (int idx = t; idx < cc_n * nt; idx += NT) {
           const int cc = idx / nt, il = idx - cc * nt;
-          Xs[idx] = a.X0[(size_t)(i0 + il) + (size_t)a.g.I * (c0 + cc)];
+          Xs[idx] = T(a.X0[(size_t)(i0 + il) + (size_t)a.g.I * (c0 + cc)]);
         }
         __syncthreads();
         for (int idx = t; idx < Mv * K1; idx += NT) {
@@ -440,8 +452,8 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<T> a) {
 // sweep 2 output: core n = Q'_n [U_p; 0]
 // ------------------------------------------------------------------------------------
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_s2_out(OutArgs<T> a) {
+template <typename S, typename T>
+__global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *V = sm<T>(smem, a.oV), *CT = sm<T>(smem, a.oCT), *CR = sm<T>(smem, a.oCR);
   Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
@@ -478,7 +490,7 @@ __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<T> a) {
     // rows (i - i0) * L + l, column l'  ->  out[l + L (i + I l')]
     for (int idx = t; idx < Mv * Ln; idx += NT) {
       const int c = idx / Mv, r = idx - c * Mv;
-      a.out[(size_t)L * i0 + r + (size_t)L * a.g.I * c] = CT[r * Ln + c];
+      a.out[(size_t)L * i0 + r + (size_t)L * a.g.I * c] = (S)CT[r * Ln + c];
     }
     __syncthreads();
   }
@@ -914,7 +926,7 @@ SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC) {
   m.oRr = (int)c.take(sizeof(T) * b * b);
   m.oTile = (int)c.take(sizeof(T) * (size_t)Tt * rho * m.ldt);
   m.oXs = (int)c.take(sizeof(T) * (size_t)CC * Tt * b);
-  m.oPs = (int)c.take(sizeof(T) * (size_t)rho * cin);
+  m.oPs = (int)c.take(std::is_same<T, double>::value ? 16 : sizeof(T) * (size_t)rho * cin);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(b, 1));
   m.oSc = (int)c.take(sizeof(T) * 2);
@@ -1027,6 +1039,7 @@ struct CorePlan {
 }  // namespace
 
 struct RoundPlan {
+  bool keep_q = true;  // store sweep-1 reflectors (rounding); the norm keeps only R
   int N = 0;
   int dtype = TT_F64;
   int nsm = 152;
@@ -1118,6 +1131,7 @@ template <typename T>
 static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false) {
   const int N = x->N;
   pl.N = N;
+  pl.keep_q = !sweep1_only;
   pl.dtype = x->dtype;
   pl.nsm = device_sm_count();
   pl.core.assign(N, CorePlan());
@@ -1160,7 +1174,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
     CorePlan &c = pl.core[n];
     max_nodes = std::max(max_nodes, c.tree.nnodes);
     max_slots = std::max(max_slots, c.tree.nslots);
-    if (n >= 1) {
+    if (n >= 1 && pl.keep_q) {
       c.refl_off = w.take(sizeof(T) * (size_t)c.I * c.K1 * c.R0, 256);
       c.tau_off = w.take(sizeof(T) * (size_t)c.I * c.R0, 256);
       const SmemTree st = smem_tree(c.R0, 1);
@@ -1176,17 +1190,29 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
   pl.off_R = w.take(sizeof(double) * max_nodes * B * B, 256);
   pl.off_C1 = w.take(sizeof(double) * max_nodes * B * B, 256);
   pl.off_C2 = w.take(sizeof(double) * max_nodes * B * B, 256);
-  pl.off_slots2 = w.take(sizeof(double) * max_slots * (B * B + B * B), 256);
-  pl.off_refl2 = w.take(sizeof(T) * max_refl2, 256);
-  pl.off_tau2 = w.take(sizeof(T) * max_tau2, 256);
+  if (pl.keep_q) {
+    pl.off_slots2 = w.take(sizeof(double) * max_slots * (B * B + B * B), 256);
+    pl.off_refl2 = w.take(sizeof(T) * max_refl2, 256);
+    pl.off_tau2 = w.take(sizeof(T) * max_tau2, 256);
+  }
   pl.off_part = w.take(sizeof(double) * 4096, 256);
   pl.total = w.off;
   return TT_OK;
 }
 
-int round_workspace(const tt_tensor *x, size_t *bytes) {
+// compute type of each precision: FP64 -> double, FP32X2 -> df32 (pairs of floats), FP32 -> float
+static int plan_for(const tt_tensor *x, int prec, RoundPlan &pl, bool sweep1_only) {
+  switch (prec) {
+    case TT_PREC_FP64: return make_plan<double>(x, pl, sweep1_only);
+    case TT_PREC_FP32X2: return make_plan<df32>(x, pl, sweep1_only);
+    case TT_PREC_FP32: return make_plan<float>(x, pl, sweep1_only);
+    default: return TT_ERR_INVALID_ARG;
+  }
+}
+
+int round_workspace(const tt_tensor *x, int prec, size_t *bytes) {
   RoundPlan pl;
-  int st = x->dtype == TT_F64 ? make_plan<double>(x, pl) : make_plan<float>(x, pl);
+  int st = plan_for(x, prec, pl, false);
   if (st) return st;
   *bytes = pl.total;
   return TT_OK;
@@ -1214,7 +1240,7 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
     TreeArgs a{};
     a.Rin = Rbase + tr.node_off[l] * B * B;
     a.Rout = Rbase + tr.node_off[l + 1] * B * B;
-    a.slots = slots + tr.slot_off[l] * ((size_t)b * b + (size_t)sm.nchunk * b);
+    a.slots = slots ? slots + tr.slot_off[l] * ((size_t)b * b + (size_t)sm.nchunk * b) : nullptr;
     a.nchild = tr.count[l];
     a.G = kG;
     a.b = b;
@@ -1296,7 +1322,7 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
   return TT_OK;
 }
 
-template <typename T>
+template <typename S, typename T>
 static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st) {
   const int N = pl.N;
   const int B = pl.bmax;
@@ -1305,15 +1331,15 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
   for (int n = N - 1; n >= 1; --n) {
     const CorePlan &c = pl.core[n];
     const SmemS1<T> m = smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8);
-    S1Args<T> a{};
-    a.X = reinterpret_cast<const T *>(x->cores[n]);
+    S1Args<S, T> a{};
+    a.X = reinterpret_cast<const S *>(x->cores[n]);
     a.g = Geom{c.I, c.P, c.Tt};
     a.b = c.R0;
     a.cin = c.R1;
     a.rho = c.K1;
     a.Pm = Pm;
-    a.refl = reinterpret_cast<T *>(ws + c.refl_off);
-    a.tau = reinterpret_cast<T *>(ws + c.tau_off);
+    a.refl = pl.keep_q ? reinterpret_cast<T *>(ws + c.refl_off) : nullptr;
+    a.tau = pl.keep_q ? reinterpret_cast<T *>(ws + c.tau_off) : nullptr;
     a.Rleaf = Rbase + c.tree.node_off[0] * B * B;
     a.CC = 8;
     a.oRr = m.oRr;
@@ -1325,14 +1351,15 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     a.oSc = m.oSc;
     a.oTau = m.oTau;
     a.ldt = m.ldt;
-    int r = set_smem(k_s1_leaf<T>, m.bytes);
+    int r = set_smem(k_s1_leaf<S, T>, m.bytes);
     if (r) return r;
     {
       TraceScope ts_(TT_K_S1_LEAF, st);
-      k_s1_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+      k_s1_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
     }
     TT_CUDA(cudaGetLastError());
-    r = tree_factor(c.tree, c.R0, c.I, c.K1, nullptr, Rbase, reinterpret_cast<double *>(ws + c.slot_off), B, st);
+    r = tree_factor(c.tree, c.R0, c.I, c.K1, nullptr, Rbase,
+                    pl.keep_q ? reinterpret_cast<double *>(ws + c.slot_off) : nullptr, B, st);
     if (r) return r;
     // move the root to the dedicated pushed-factor region so that the next core's leaves
     // can overwrite the tree levels
@@ -1345,7 +1372,7 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
   return TT_OK;
 }
 
-template <typename T>
+template <typename S, typename T>
 static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_tensor *out, unsigned char *ws,
                      cudaStream_t st) {
   const int N = pl.N;
@@ -1359,7 +1386,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     k_init_ctl<<<1, 32, 0, st>>>(dL, N, dstatus);
   }
   TT_CUDA(cudaGetLastError());
-  int r = sweep1<T>(pl, x, ws, st);
+  int r = sweep1<S, T>(pl, x, ws, st);
   if (r) return r;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
   double *C1 = reinterpret_cast<double *>(ws + pl.off_C1);
@@ -1382,7 +1409,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     {
       const int mode = n == 0 ? 1 : 0;
       const SmemS2<T> m = smem_s2<T>(mode, n == 0 ? 1 : c.R0, K1, n == 0 ? 1 : c.K0, c.Tt, c.R1, 8);
-      S2Args<T> a{};
+      S2Args<S, T> a{};
       a.mode = mode;
       a.g = Geom{c.I, c.P, c.Tt};
       if (n >= 1) {
@@ -1394,7 +1421,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
         a.Lcur = dL + n;
       } else {
         a.b1 = 1;
-        a.X0 = reinterpret_cast<const T *>(x->cores[0]);
+        a.X0 = reinterpret_cast<const S *>(x->cores[0]);
         a.cin = c.R1;
         a.Pm = N > 1 ? P1 : nullptr;
         a.CC = 8;
@@ -1416,11 +1443,11 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.oTv = m.oTv;
       a.ldq = m.ldq;
       a.ldv = m.ldv;
-      r = set_smem(k_s2_leaf<T>, m.bytes);
+      r = set_smem(k_s2_leaf<S, T>, m.bytes);
       if (r) return r;
       {
         TraceScope ts_(TT_K_S2_LEAF, st);
-        k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+        k_s2_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
       }
       TT_CUDA(cudaGetLastError());
     }
@@ -1459,7 +1486,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     if (r) return r;
     {
       const SmemOut<T> m = smem_out<T>(K1, n == 0 ? 1 : c.K0, c.Tt);
-      OutArgs<T> a{};
+      OutArgs<S, T> a{};
       a.g = Geom{c.I, c.P, c.Tt};
       a.vrefl = refl2;
       a.vtau = tau2;
@@ -1468,7 +1495,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.Lnext = dL + n + 1;
       a.Uleaf = C2 + c.tree.node_off[0] * (size_t)B * B;
       a.ldc = B;
-      a.out = reinterpret_cast<T *>(out->cores[n]);
+      a.out = reinterpret_cast<S *>(out->cores[n]);
       a.oV = m.oV;
       a.oCT = m.oCT;
       a.oCR = m.oCR;
@@ -1477,11 +1504,11 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.oSc = m.oSc;
       a.oTau = m.oTau;
       a.ldv = m.ldv;
-      r = set_smem(k_s2_out<T>, m.bytes);
+      r = set_smem(k_s2_out<S, T>, m.bytes);
       if (r) return r;
       {
         TraceScope ts_(TT_K_S2_OUT, st);
-        k_s2_out<T><<<c.P, NT, m.bytes, st>>>(a);
+        k_s2_out<S, T><<<c.P, NT, m.bytes, st>>>(a);
       }
       TT_CUDA(cudaGetLastError());
     }
@@ -1493,7 +1520,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
                    reinterpret_cast<double *>(ws + c.slot_off), B, st);
     if (r) return r;
     const SmemS2<T> m = smem_s2<T>(2, c.R0, 1, c.K0, c.Tt, 1, 8);
-    S2Args<T> a{};
+    S2Args<S, T> a{};
     a.mode = 2;
     a.g = Geom{c.I, c.P, c.Tt};
     a.qrefl = reinterpret_cast<const T *>(ws + c.refl_off);
@@ -1503,7 +1530,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     a.Cleaf = C1 + c.tree.node_off[0] * (size_t)B * B;
     a.ldc = B;
     a.Lcur = dL + N - 1;
-    a.out = reinterpret_cast<T *>(out->cores[N - 1]);
+    a.out = reinterpret_cast<S *>(out->cores[N - 1]);
     a.oQ = m.oQ;
     a.oCT = m.oCT;
     a.oCR = m.oCR;
@@ -1517,11 +1544,11 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     a.oTv = m.oTv;
     a.ldq = m.ldq;
     a.ldv = m.ldv;
-    r = set_smem(k_s2_leaf<T>, m.bytes);
+    r = set_smem(k_s2_leaf<S, T>, m.bytes);
     if (r) return r;
     {
       TraceScope ts_(TT_K_S2_LEAF, st);
-      k_s2_leaf<T><<<c.P, NT, m.bytes, st>>>(a);
+      k_s2_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
     }
     TT_CUDA(cudaGetLastError());
   }
@@ -1536,7 +1563,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   return TT_OK;
 }
 
-int round_run(const tt_tensor *x, double eps, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
   if (x->N == 1) {
     const size_t es = x->dtype == TT_F64 ? 8 : 4;
     TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDeviceToDevice, st));
@@ -1545,25 +1572,31 @@ int round_run(const tt_tensor *x, double eps, tt_tensor *out, void *ws, size_t w
     return TT_OK;
   }
   RoundPlan pl;
-  int r = x->dtype == TT_F64 ? make_plan<double>(x, pl) : make_plan<float>(x, pl);
+  int r = plan_for(x, prec, pl, false);
   if (r) return r;
   if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
   unsigned char *w = reinterpret_cast<unsigned char *>(ws);
-  return x->dtype == TT_F64 ? run_round<double>(pl, x, eps, out, w, st) : run_round<float>(pl, x, eps, out, w, st);
+  switch (prec) {
+    case TT_PREC_FP64: return run_round<double, double>(pl, x, eps, out, w, st);
+    case TT_PREC_FP32X2: return run_round<float, df32>(pl, x, eps, out, w, st);
+    default: return run_round<float, float>(pl, x, eps, out, w, st);
+  }
 }
+
+static int norm_prec(const tt_tensor *x) { return x->dtype == TT_F64 ? TT_PREC_FP64 : TT_PREC_FP32X2; }
 
 int norm_workspace(const tt_tensor *x, size_t *bytes) {
   RoundPlan pl;
-  int st = x->dtype == TT_F64 ? make_plan<double>(x, pl, true) : make_plan<float>(x, pl, true);
+  int st = plan_for(x, norm_prec(x), pl, true);
   if (st) return st;
   *bytes = pl.total;
   return TT_OK;
 }
 
-template <typename T>
+template <typename S, typename T>
 static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, unsigned char *ws, cudaStream_t st) {
   const int N = pl.N;
-  int r = N > 1 ? sweep1<T>(pl, x, ws, st) : TT_OK;
+  int r = N > 1 ? sweep1<S, T>(pl, x, ws, st) : TT_OK;
   if (r) return r;
   const CorePlan &c0 = pl.core[0];
   double *part = reinterpret_cast<double *>(ws + pl.off_part);
@@ -1575,7 +1608,7 @@ static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, uns
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (total + NT - 1) / NT));
   {
     TraceScope ts_(TT_K_MISC, st);
-    k_push_sumsq<T><<<blocks, NT, 0, st>>>(reinterpret_cast<const T *>(x->cores[0]), c0.I, cin, K, Pm, part);
+    k_push_sumsq<S><<<blocks, NT, 0, st>>>(reinterpret_cast<const S *>(x->cores[0]), c0.I, cin, K, Pm, part);
   }
   TT_CUDA(cudaGetLastError());
   {
@@ -1590,11 +1623,12 @@ static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, uns
 
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st) {
   RoundPlan pl;
-  int r = x->dtype == TT_F64 ? make_plan<double>(x, pl, true) : make_plan<float>(x, pl, true);
+  int r = plan_for(x, norm_prec(x), pl, true);
   if (r) return r;
   if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
   unsigned char *w = reinterpret_cast<unsigned char *>(ws);
-  return x->dtype == TT_F64 ? run_norm<double>(pl, x, result, w, st) : run_norm<float>(pl, x, result, w, st);
+  return x->dtype == TT_F64 ? run_norm<double, double>(pl, x, result, w, st)
+                            : run_norm<float, df32>(pl, x, result, w, st);
 }
 
 }  // namespace ttgb

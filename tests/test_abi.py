@@ -65,8 +65,8 @@ def test_invalid_tensors_rejected(lib, I, R, dtype):
     x = make_desc(I, R, dtype)
     out = make_desc(I, [1] * (len(I) + 1), dtype)
     n = ctypes.c_size_t(0)
-    assert lib.tt_round_workspace_size(ctypes.byref(x), ctypes.byref(n)) == 1
-    assert lib.tt_round(ctypes.byref(x), 1e-6, ctypes.byref(out), None, 0, None) == 1
+    assert lib.tt_round_workspace_size(ctypes.byref(x), 0, ctypes.byref(n)) == 1
+    assert lib.tt_round(ctypes.byref(x), 1e-6, 0, ctypes.byref(out), None, 0, None) == 1
     assert lib.tt_add(ctypes.byref(x), ctypes.byref(x), ctypes.byref(out), None) == 1
 
 
@@ -74,20 +74,26 @@ def test_invalid_eps_and_mismatch_rejected(lib):
     x = make_desc([4, 5, 6], [1, 2, 3, 1])
     out = make_desc([4, 5, 6], [1, 1, 1, 1])
     for eps in [-1.0, float("nan"), float("inf")]:
-        assert lib.tt_round(ctypes.byref(x), eps, ctypes.byref(out), None, 0, None) == 1
+        assert lib.tt_round(ctypes.byref(x), eps, 0, ctypes.byref(out), None, 0, None) == 1
     other = make_desc([4, 5, 7], [1, 2, 3, 1])
     res = ctypes.c_double(0)
     assert lib.tt_dot(ctypes.byref(x), ctypes.byref(other), ctypes.byref(res), None, 0, None) == 1
     assert lib.tt_hadamard(ctypes.byref(x), ctypes.byref(other), ctypes.byref(out), None) == 1
-    assert lib.tt_round(ctypes.byref(x), 1e-3, None, None, 0, None) == 1
+    assert lib.tt_round(ctypes.byref(x), 1e-3, 0, None, None, 0, None) == 1
     nullc = make_desc([4, 5, 6], [1, 2, 3, 1], null_core=True)
-    assert lib.tt_round(ctypes.byref(nullc), 1e-3, ctypes.byref(out), None, 0, None) == 1
+    assert lib.tt_round(ctypes.byref(nullc), 1e-3, 0, ctypes.byref(out), None, 0, None) == 1
+    # precision must match the element type
+    for prec in [2, 3, 7, -1]:
+        assert lib.tt_round(ctypes.byref(x), 1e-3, prec, ctypes.byref(out), None, 0, None) == 1
+    x32 = make_desc([4, 5, 6], [1, 2, 3, 1], dtype=1)
+    out32 = make_desc([4, 5, 6], [1, 1, 1, 1], dtype=1)
+    assert lib.tt_round(ctypes.byref(x32), 1e-3, 1, ctypes.byref(out32), None, 0, None) == 1
 
 
 def test_rank_above_maximum_unsupported(lib):
     x = make_desc([300, 300], [1, 200, 1])
     n = ctypes.c_size_t(0)
-    assert lib.tt_round_workspace_size(ctypes.byref(x), ctypes.byref(n)) == 6
+    assert lib.tt_round_workspace_size(ctypes.byref(x), 0, ctypes.byref(n)) == 6
 
 
 def test_missing_library_fails_loudly(tmp_path):
@@ -101,5 +107,8 @@ def test_workspace_size_query_has_no_device_side_effects(lib):
     # the size query is pure host arithmetic over the shapes
     x = make_desc([64, 32, 16], [1, 8, 4, 1])
     n = ctypes.c_size_t(0)
-    st = lib.tt_round_workspace_size(ctypes.byref(x), ctypes.byref(n))
+    st = lib.tt_round_workspace_size(ctypes.byref(x), 0, ctypes.byref(n))
     assert st == 0 and n.value > 0
+    x32 = make_desc([64, 32, 16], [1, 8, 4, 1], dtype=1)
+    for prec in [0, 2, 3]:
+        assert lib.tt_round_workspace_size(ctypes.byref(x32), prec, ctypes.byref(n)) == 0 and n.value > 0
