@@ -111,12 +111,33 @@ int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void
              void *stream);
 
 /*
- * Rounds `count` independent tensors with one shared workspace, queueing them
- * back to back on `stream` (each entry as in tt_round; eps[k] per tensor).
- * workspace_bytes must cover the largest tt_round_workspace_size of the batch.
+ * Batched rounding of `count` independent tensors (each as in tt_round, eps[k]
+ * per tensor, one precision for all).  The batch is spread over up to
+ * TT_BATCH_SLOTS internal CUDA streams forked from `stream` and joined back
+ * into it; tensor k runs on slot k mod TT_BATCH_SLOTS, in order, and each slot
+ * owns one region of the workspace.  The library creates those streams and
+ * their events once per device on first use and keeps them until exit.
  */
+#define TT_BATCH_SLOTS 16
+
+/* Workspace bytes for a batch (slots plus device space for ranks and status). */
+int tt_round_batched_workspace_size(int32_t count, const tt_tensor *xs, int precision, size_t *bytes);
+
+/* Synchronous: fills outs[k].R; returns the first non-OK status of the batch. */
 int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
                      void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Asynchronous form of tt_round_batched: queues everything on `stream` (and the
+ * slot streams joined into it) and returns without synchronizing, so the call
+ * can be captured into a CUDA graph.  Ranks of tensor k go to the device array
+ * ranks_dev at offset sum_{j<k} (xs[j].N + 1), its status word to
+ * status_dev[k] (both caller-owned device int32 arrays); outs[k].R is not
+ * written.  Shapes, pointers and eps are read at call time.
+ */
+int tt_round_batched_async(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                           int32_t *ranks_dev, int32_t *status_dev, void *workspace, size_t workspace_bytes,
+                           void *stream);
 
 /*
  * Summation (Sec. 3.2.1): Z = A + B.  Interior slices are block diagonal

@@ -21,7 +21,7 @@ import torch
 from . import _native
 from ._native import build  # noqa: F401  (re-export)
 
-__all__ = ["DeviceTT", "build", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard", "tt_dot", "tt_norm",
+__all__ = ["DeviceTT", "Batch", "build", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard", "tt_dot", "tt_norm",
            "TTError", "from_host", "to_host", "trace", "trace_read"]
 
 _DTYPES = {torch.float64: 0, torch.float32: 1}
@@ -138,30 +138,71 @@ def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tens
     return DeviceTT(list(x.I), R, cores)
 
 
+class Batch:
+    """A prepared batch: descriptors, output buffers and workspace of a list of tensors.
+
+    run() rounds the whole batch synchronously; enqueue() queues it without a host
+    synchronization (ranks stay on the device), so it can be captured in a CUDA graph;
+    ranks() / outputs() read the results after the queued work has finished."""
+
+    def __init__(self, xs: Sequence[DeviceTT], eps: Sequence[float], precision: str = "default"):
+        for x in xs:
+            _validate(x)
+        lib = _native.load()
+        self.xs = list(xs)
+        self.eps = (ctypes.c_double * max(len(xs), 1))(*[float(v) for v in eps])
+        self.prec = PRECISIONS[precision]
+        dev = xs[0].cores[0].device
+        self.descs = [_Desc(x.I, x.R, x.cores, x.dtype) for x in xs]
+        self.outs = [[torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()] for x in xs]
+        self.odescs = [_Desc(x.I, [1] * (x.N + 1), o, x.dtype) for x, o in zip(xs, self.outs)]
+        self.arr_in = (_native.TTTensor * len(xs))(*[d.s for d in self.descs])
+        self.arr_out = (_native.TTTensor * len(xs))(*[d.s for d in self.odescs])
+        n = ctypes.c_size_t(0)
+        _check(lib.tt_round_batched_workspace_size(len(xs), self.arr_in, self.prec, ctypes.byref(n)),
+               "tt_round_batched_workspace_size")
+        self.ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+        self.ranks_dev = torch.zeros(sum(x.N + 1 for x in xs), dtype=torch.int32, device=dev)
+        self.status_dev = torch.zeros(len(xs), dtype=torch.int32, device=dev)
+
+    def run(self, stream=None) -> List[DeviceTT]:
+        lib = _native.load()
+        _check(lib.tt_round_batched(len(self.xs), self.arr_in, self.eps, self.prec, self.arr_out,
+                                    ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws.numel()),
+                                    _stream(stream)), "tt_round_batched")
+        res = []
+        for k, x in enumerate(self.xs):
+            R = [int(self.arr_out[k].R[i]) for i in range(x.N + 1)]
+            res.append(DeviceTT(list(x.I), R, [self.outs[k][n][: R[n] * x.I[n] * R[n + 1]] for n in range(x.N)]))
+        return res
+
+    def enqueue(self, stream=None) -> None:
+        lib = _native.load()
+        _check(lib.tt_round_batched_async(len(self.xs), self.arr_in, self.eps, self.prec, self.arr_out,
+                                          ctypes.c_void_p(self.ranks_dev.data_ptr()),
+                                          ctypes.c_void_p(self.status_dev.data_ptr()),
+                                          ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws.numel()),
+                                          _stream(stream)), "tt_round_batched_async")
+
+    def outputs(self) -> List[DeviceTT]:
+        status = self.status_dev.tolist()
+        for st in status:
+            _check(st, "tt_round_batched_async")
+        ranks = self.ranks_dev.tolist()
+        res, off = [], 0
+        for k, x in enumerate(self.xs):
+            R = ranks[off: off + x.N + 1]
+            off += x.N + 1
+            res.append(DeviceTT(list(x.I), R, [self.outs[k][n][: R[n] * x.I[n] * R[n + 1]] for n in range(x.N)]))
+        return res
+
+
 def tt_round_batched(xs: Sequence[DeviceTT], eps: Sequence[float], stream=None,
                      precision: str = "default") -> List[DeviceTT]:
-    """Rounds several independent tensors with one call (shared workspace)."""
-    lib = _native.load()
+    """Rounds several independent tensors with one call (spread over internal streams)."""
     if not xs:
         return []
-    for x in xs:
-        _validate(x)
-    dev = xs[0].cores[0].device
-    descs = [_Desc(x.I, x.R, x.cores, x.dtype) for x in xs]
-    need = max(round_workspace_size(x, precision) for x in xs)
-    ws = _workspace(need, dev)
-    outs = [[torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()] for x in xs]
-    odescs = [_Desc(x.I, [1] * (x.N + 1), o, x.dtype) for x, o in zip(xs, outs)]
-    arr_in = (_native.TTTensor * len(xs))(*[d.s for d in descs])
-    arr_out = (_native.TTTensor * len(xs))(*[d.s for d in odescs])
-    e = (ctypes.c_double * len(xs))(*[float(v) for v in eps])
-    _check(lib.tt_round_batched(len(xs), arr_in, e, PRECISIONS[precision], arr_out, ctypes.c_void_p(ws.data_ptr()),
-                                ctypes.c_size_t(ws.numel()), _stream(stream)), "tt_round_batched")
-    res = []
-    for k, x in enumerate(xs):
-        R = [int(arr_out[k].R[i]) for i in range(x.N + 1)]
-        res.append(DeviceTT(list(x.I), R, [outs[k][n][: R[n] * x.I[n] * R[n + 1]] for n in range(x.N)]))
-    return res
+    return Batch(xs, eps, precision).run(stream)
 
 
 def tt_add(a: DeviceTT, b: DeviceTT, stream=None) -> DeviceTT:

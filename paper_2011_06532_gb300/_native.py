@@ -75,7 +75,7 @@ class TTTensor(ctypes.Structure):
 EXPORTS = [
     "tt_round_workspace_size", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard",
     "tt_dot_workspace_size", "tt_dot", "tt_norm_workspace_size", "tt_norm", "tt_status_string",
-    "tt_trace", "tt_trace_read", "tt_dot_noalloc",
+    "tt_trace", "tt_trace_read", "tt_dot_noalloc", "tt_round_batched_workspace_size", "tt_round_batched_async",
 ]
 KERNEL_KINDS = ["s1_leaf", "tree_factor", "tree_apply", "s2_leaf", "s2_out", "svd", "add", "hadamard", "dot", "misc"]
 
@@ -98,6 +98,8 @@ def load(path: str | None = None):
         "tt_round_workspace_size": [T, ctypes.c_int, sz],
         "tt_round": [T, ctypes.c_double, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
         "tt_round_batched": [ctypes.c_int32, T, dp, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_round_batched_workspace_size": [ctypes.c_int32, T, ctypes.c_int, sz],
+        "tt_round_batched_async": [ctypes.c_int32, T, dp, ctypes.c_int, T, vp, vp, vp, ctypes.c_size_t, vp],
         "tt_add": [T, T, T, vp],
         "tt_hadamard": [T, T, T, vp],
         "tt_dot_workspace_size": [T, T, sz],

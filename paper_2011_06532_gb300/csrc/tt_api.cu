@@ -150,8 +150,65 @@ int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void
   return ttgb::round_run(x, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
 }
 
-int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
-                     void *workspace, size_t workspace_bytes, void *stream) {
+namespace {
+
+struct BatchStreams {
+  bool ready = false;
+  cudaStream_t s[TT_BATCH_SLOTS];
+  cudaEvent_t fork;
+  cudaEvent_t join[TT_BATCH_SLOTS];
+};
+constexpr int kMaxDevices = 64;
+std::mutex g_batch_mu;
+BatchStreams g_batch[kMaxDevices];
+
+int batch_streams(BatchStreams **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TT_ERR_CUDA;
+  if (dev < 0 || dev >= kMaxDevices) return TT_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> g(g_batch_mu);
+  BatchStreams &b = g_batch[dev];
+  if (!b.ready) {
+    for (int k = 0; k < TT_BATCH_SLOTS; ++k) {
+      if (cudaStreamCreateWithFlags(&b.s[k], cudaStreamNonBlocking) != cudaSuccess) return TT_ERR_CUDA;
+      if (cudaEventCreateWithFlags(&b.join[k], cudaEventDisableTiming) != cudaSuccess) return TT_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) != cudaSuccess) return TT_ERR_CUDA;
+    b.ready = true;
+  }
+  *out = &b;
+  return TT_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct BatchLayout {
+  int slots = 0;
+  size_t slot_bytes = 0, ranks_off = 0, status_off = 0, total = 0;
+};
+
+int batch_layout(int32_t count, const tt_tensor *xs, int precision, BatchLayout *lay) {
+  size_t mx = 0, nranks = 0;
+  for (int k = 0; k < count; ++k) {
+    const int prec = resolve_prec(&xs[k], precision);
+    if (prec < 0) return TT_ERR_INVALID_ARG;
+    size_t b = 0;
+    if (xs[k].N > 1) {
+      const int st = ttgb::round_workspace(&xs[k], prec, &b);
+      if (st) return st;
+    }
+    mx = b > mx ? b : mx;
+    nranks += (size_t)xs[k].N + 1;
+  }
+  lay->slots = count < TT_BATCH_SLOTS ? count : TT_BATCH_SLOTS;
+  lay->slot_bytes = align256(mx ? mx : 256);
+  lay->ranks_off = lay->slot_bytes * lay->slots;
+  lay->status_off = lay->ranks_off + align256(sizeof(int32_t) * (nranks ? nranks : 1));
+  lay->total = lay->status_off + align256(sizeof(int32_t) * (count ? count : 1));
+  return TT_OK;
+}
+
+int check_batch(int32_t count, const tt_tensor *xs, const double *eps, tt_tensor *outs, int precision) {
   if (count < 0 || (count > 0 && (!xs || !eps || !outs))) return TT_ERR_INVALID_ARG;
   for (int k = 0; k < count; ++k) {
     if (!valid_tensor(&xs[k]) || !valid_out(&xs[k], &outs[k]) || !(eps[k] >= 0.0) || !isfinite(eps[k]))
@@ -159,10 +216,94 @@ int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int 
     if (resolve_prec(&xs[k], precision) < 0) return TT_ERR_INVALID_ARG;
     if (!ranks_supported(&xs[k])) return TT_ERR_UNSUPPORTED;
   }
+  return TT_OK;
+}
+
+int batch_enqueue(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                  int32_t *ranks_dev, int32_t *status_dev, unsigned char *ws, const BatchLayout &lay,
+                  cudaStream_t stream) {
+  if (count == 0) return TT_OK;
+  BatchStreams *bs = nullptr;
+  int st = batch_streams(&bs);
+  if (st) return st;
+  if (cudaEventRecord(bs->fork, stream) != cudaSuccess) return TT_ERR_CUDA;
+  for (int s = 0; s < lay.slots; ++s)
+    if (cudaStreamWaitEvent(bs->s[s], bs->fork, 0) != cudaSuccess) return TT_ERR_CUDA;
+  size_t roff = 0;
   for (int k = 0; k < count; ++k) {
-    const int st = ttgb::round_run(&xs[k], eps[k], resolve_prec(&xs[k], precision), &outs[k], workspace,
-                                   workspace_bytes, as_stream(stream));
+    const int slot = k % lay.slots;
+    st = ttgb::round_enqueue(&xs[k], eps[k], resolve_prec(&xs[k], precision), &outs[k],
+                             ws + (size_t)slot * lay.slot_bytes, lay.slot_bytes, bs->s[slot], ranks_dev + roff,
+                             status_dev + k);
     if (st) return st;
+    roff += (size_t)xs[k].N + 1;
+  }
+  for (int s = 0; s < lay.slots; ++s) {
+    if (cudaEventRecord(bs->join[s], bs->s[s]) != cudaSuccess) return TT_ERR_CUDA;
+    if (cudaStreamWaitEvent(stream, bs->join[s], 0) != cudaSuccess) return TT_ERR_CUDA;
+  }
+  return TT_OK;
+}
+
+}  // namespace
+
+int tt_round_batched_workspace_size(int32_t count, const tt_tensor *xs, int precision, size_t *bytes) {
+  if (count < 0 || (count > 0 && !xs) || !bytes) return TT_ERR_INVALID_ARG;
+  for (int k = 0; k < count; ++k) {
+    if (!valid_tensor(&xs[k])) return TT_ERR_INVALID_ARG;
+    if (!ranks_supported(&xs[k])) return TT_ERR_UNSUPPORTED;
+  }
+  BatchLayout lay;
+  const int st = batch_layout(count, xs, precision, &lay);
+  if (st) return st;
+  *bytes = lay.total;
+  return TT_OK;
+}
+
+int tt_round_batched_async(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                           int32_t *ranks_dev, int32_t *status_dev, void *workspace, size_t workspace_bytes,
+                           void *stream) {
+  int st = check_batch(count, xs, eps, outs, precision);
+  if (st) return st;
+  if (count > 0 && (!ranks_dev || !status_dev)) return TT_ERR_INVALID_ARG;
+  BatchLayout lay;
+  st = batch_layout(count, xs, precision, &lay);
+  if (st) return st;
+  if (count > 0 && (!workspace || workspace_bytes < lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255)))
+    return TT_ERR_WORKSPACE;
+  return batch_enqueue(count, xs, eps, precision, outs, ranks_dev, status_dev,
+                       reinterpret_cast<unsigned char *>(workspace), lay, as_stream(stream));
+}
+
+int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+  int st = check_batch(count, xs, eps, outs, precision);
+  if (st) return st;
+  if (count == 0) return TT_OK;
+  BatchLayout lay;
+  st = batch_layout(count, xs, precision, &lay);
+  if (st) return st;
+  if (!workspace || workspace_bytes < lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return TT_ERR_WORKSPACE;
+  unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
+  int32_t *ranks_dev = reinterpret_cast<int32_t *>(ws + lay.ranks_off);
+  int32_t *status_dev = reinterpret_cast<int32_t *>(ws + lay.status_off);
+  cudaStream_t s = as_stream(stream);
+  st = batch_enqueue(count, xs, eps, precision, outs, ranks_dev, status_dev, ws, lay, s);
+  if (st) return st;
+  size_t nranks = 0;
+  for (int k = 0; k < count; ++k) nranks += (size_t)xs[k].N + 1;
+  std::vector<int32_t> ranks(nranks), status(count);
+  if (cudaMemcpyAsync(ranks.data(), ranks_dev, sizeof(int32_t) * nranks, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return TT_ERR_CUDA;
+  if (cudaMemcpyAsync(status.data(), status_dev, sizeof(int32_t) * count, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return TT_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TT_ERR_CUDA;
+  size_t roff = 0;
+  for (int k = 0; k < count; ++k) {
+    if (status[k]) return status[k];
+    for (int n = 0; n <= xs[k].N; ++n) outs[k].R[n] = ranks[roff + n];
+    roff += (size_t)xs[k].N + 1;
   }
   return TT_OK;
 }

@@ -10,6 +10,8 @@ namespace ttgb {
 
 int round_workspace(const tt_tensor *x, int prec, size_t *bytes);
 int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st);
+int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes,
+                  cudaStream_t st, int *ranks_dev, int *status_dev);
 int norm_workspace(const tt_tensor *x, size_t *bytes);
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st);
 

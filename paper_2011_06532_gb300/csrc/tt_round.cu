@@ -48,9 +48,12 @@ struct S1Args {
   T *tau;            // I x b
   double *Rleaf;     // P x b*b row-major
   int CC;            // push chunk width
-  // shared-memory offsets (bytes)
+  // shared-memory offsets (bytes); a negative offset -1-e places the buffer at element e
+  // of this leaf's region of the global scratch (used when shared memory is short)
   int oRr, oTile, oXs, oPs, oRed, oW, oSc, oTau;
   int ldt;
+  T *gscr;
+  size_t gstride;
 };
 
 struct TreeArgs {
@@ -97,6 +100,8 @@ struct S2Args {
   S *out;               // last core output (L x I x 1)
   int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv;
   int ldq, ldv;
+  T *gscr;
+  size_t gstride;
 };
 
 template <typename S, typename T>
@@ -112,6 +117,8 @@ struct OutArgs {
   S *out;               // output core n: L[n] x I x L[n+1]
   int oV, oCT, oCR, oRed, oW, oSc, oTau;
   int ldv;
+  T *gscr;
+  size_t gstride;
 };
 
 struct SvdArgs {
@@ -141,6 +148,12 @@ __device__ __forceinline__ T *sm(unsigned char *base, int off) {
 
 __device__ __forceinline__ int dyn(const int *p, int v) { return p ? *p : v; }
 
+// buffer at shared offset off, or (off < 0) at element -1-off of this CTA's global scratch
+template <typename T>
+__device__ __forceinline__ T *buf(unsigned char *base, int off, T *gscr, size_t gstride) {
+  return off >= 0 ? reinterpret_cast<T *>(base + off) : gscr + (size_t)blockIdx.x * gstride + (size_t)(-1 - off);
+}
+
 // rows of the stacked matrix owned by leaf range [l0, l1)
 __device__ __forceinline__ int64_t rows_of_leaves(int64_t I, int P, int l0, int l1, int rho) {
   return (leaf_begin(I, P, l1) - leaf_begin(I, P, l0)) * (int64_t)rho;
@@ -153,7 +166,8 @@ __device__ __forceinline__ int64_t rows_of_leaves(int64_t I, int P, int l0, int 
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *Rr = sm<T>(smem, a.oRr), *tile = sm<T>(smem, a.oTile), *Xs = sm<T>(smem, a.oXs), *Ps = sm<T>(smem, a.oPs);
+  T *Rr = buf<T>(smem, a.oRr, a.gscr, a.gstride), *tile = sm<T>(smem, a.oTile), *Xs = sm<T>(smem, a.oXs);
+  T *Ps = buf<T>(smem, a.oPs, a.gscr, a.gstride);
   Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
   T *taus = sm<T>(smem, a.oTau);
   const int p = blockIdx.x, t = threadIdx.x;
@@ -348,8 +362,9 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *Q = sm<T>(smem, a.oQ), *CT = sm<T>(smem, a.oCT), *CR = sm<T>(smem, a.oCR), *Rr = sm<T>(smem, a.oRr);
-  T *Xs = sm<T>(smem, a.oXs), *Ps = sm<T>(smem, a.oPs);
+  T *Q = sm<T>(smem, a.oQ), *CT = sm<T>(smem, a.oCT);
+  T *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride), *Rr = buf<T>(smem, a.oRr, a.gscr, a.gstride);
+  T *Xs = sm<T>(smem, a.oXs), *Ps = buf<T>(smem, a.oPs, a.gscr, a.gstride);
   Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
   T *tq = sm<T>(smem, a.oTq), *tv = sm<T>(smem, a.oTv);
   const int p = blockIdx.x, t = threadIdx.x;
@@ -455,7 +470,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *V = sm<T>(smem, a.oV), *CT = sm<T>(smem, a.oCT), *CR = sm<T>(smem, a.oCR);
+  T *V = sm<T>(smem, a.oV), *CT = sm<T>(smem, a.oCT), *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride);
   Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
   T *tv = sm<T>(smem, a.oTau);
   const int p = blockIdx.x, t = threadIdx.x;
@@ -912,40 +927,60 @@ int leaves_for(int64_t I, int nsm) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(I, target));
 }
 
-template <typename T>
-struct SmemS1 {
-  int oRr, oTile, oXs, oPs, oRed, oW, oSc, oTau, ldt;
-  size_t bytes;
+// a buffer of `elems` elements either carved from shared memory or, when spilled, placed
+// at the next free element of the per-leaf global scratch (negative encoded offset)
+struct Place {
+  Carve c;
+  bool spill;
+  size_t g = 0;
+  int take(size_t bytes, size_t elems, bool spillable) {
+    if (spill && spillable) {
+      const int off = -1 - (int)g;
+      g += elems;
+      return off;
+    }
+    return (int)c.take(bytes);
+  }
 };
 
 template <typename T>
-SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC) {
+struct SmemS1 {
+  int oRr, oTile, oXs, oPs, oRed, oW, oSc, oTau, ldt;
+  size_t bytes, gstride;
+};
+
+template <typename T>
+SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false) {
   SmemS1<T> m;
-  Carve c;
+  Place pl{Carve(), spill};
+  Carve &c = pl.c;
   m.ldt = b + 1;
-  m.oRr = (int)c.take(sizeof(T) * b * b);
+  m.oRr = pl.take(sizeof(T) * b * b, (size_t)b * b, true);
   m.oTile = (int)c.take(sizeof(T) * (size_t)Tt * rho * m.ldt);
   m.oXs = (int)c.take(sizeof(T) * (size_t)CC * Tt * b);
-  m.oPs = (int)c.take(std::is_same<T, double>::value ? 16 : sizeof(T) * (size_t)rho * cin);
+  m.oPs = std::is_same<T, double>::value ? (int)c.take(16)
+                                          : pl.take(sizeof(T) * (size_t)rho * cin, (size_t)rho * cin, true);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(b, 1));
   m.oSc = (int)c.take(sizeof(T) * 2);
   m.oTau = (int)c.take(sizeof(T) * b);
   m.bytes = c.off;
+  m.gstride = pl.g;
   return m;
 }
 
 template <typename T>
 struct SmemS2 {
   int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv, ldq, ldv;
-  size_t bytes;
+  size_t bytes, gstride;
 };
 
 // mode A/last: b1 = R_n, K1 = K_{n+1}, Lmax = max rows per slice of V(Y_n) (<= K_n)
 template <typename T>
-SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC) {
+SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC, bool spill = false) {
   SmemS2<T> m;
-  Carve c;
+  Place pl{Carve(), spill};
+  Carve &c = pl.c;
   m.ldq = b1 + 1;
   m.ldv = K1 + 1;
   size_t qrows = mode == 1 ? 0 : (size_t)Tt * K1;
@@ -953,38 +988,41 @@ SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC) {
   size_t qbytes = std::max(qrows * m.ldq, mode == 2 ? 0 : vrows * m.ldv) * sizeof(T);
   m.oQ = (int)c.take(qbytes);
   m.oCT = (int)c.take(sizeof(T) * (mode == 1 ? 1 : qrows * Lmax));
-  m.oCR = (int)c.take(sizeof(T) * (mode == 1 ? 1 : (size_t)b1 * Lmax));
-  m.oRr = (int)c.take(sizeof(T) * (size_t)K1 * K1);
+  m.oCR = pl.take(sizeof(T) * (mode == 1 ? 1 : (size_t)b1 * Lmax), mode == 1 ? 1 : (size_t)b1 * Lmax, true);
+  m.oRr = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, true);
   m.oXs = (int)c.take(sizeof(T) * (mode == 1 ? (size_t)CC * Tt : 1));
-  m.oPs = (int)c.take(sizeof(T) * (mode == 1 ? (size_t)K1 * cin : 1));
+  m.oPs = pl.take(sizeof(T) * (mode == 1 ? (size_t)K1 * cin : 1), mode == 1 ? (size_t)K1 * cin : 1, true);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(std::max(b1, K1), Lmax));
   m.oSc = (int)c.take(sizeof(T) * 2);
   m.oTq = (int)c.take(sizeof(T) * std::max(b1, 1));
   m.oTv = (int)c.take(sizeof(T) * K1);
   m.bytes = c.off;
+  m.gstride = pl.g;
   return m;
 }
 
 template <typename T>
 struct SmemOut {
   int oV, oCT, oCR, oRed, oW, oSc, oTau, ldv;
-  size_t bytes;
+  size_t bytes, gstride;
 };
 
 template <typename T>
-SmemOut<T> smem_out(int K1, int Lmax, int Tt) {
+SmemOut<T> smem_out(int K1, int Lmax, int Tt, bool spill = false) {
   SmemOut<T> m;
-  Carve c;
+  Place pl{Carve(), spill};
+  Carve &c = pl.c;
   m.ldv = K1 + 1;
   m.oV = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * m.ldv);
   m.oCT = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * K1);
-  m.oCR = (int)c.take(sizeof(T) * (size_t)K1 * K1);
+  m.oCR = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, true);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(K1, 1));
   m.oSc = (int)c.take(sizeof(T) * 2);
   m.oTau = (int)c.take(sizeof(T) * K1);
   m.bytes = c.off;
+  m.gstride = pl.g;
   return m;
 }
 
@@ -1032,6 +1070,7 @@ struct CorePlan {
   int R0 = 1, R1 = 1;  // input ranks
   int K0 = 1, K1 = 1;  // ranks after sweep 1
   int P = 1, Tt = 1;
+  bool spill = false;  // running factor / carried block in global scratch
   Tree tree;
   size_t refl_off = 0, tau_off = 0, slot_off = 0;  // sweep-1 storage (n >= 1)
 };
@@ -1040,6 +1079,8 @@ struct CorePlan {
 
 struct RoundPlan {
   bool keep_q = true;  // store sweep-1 reflectors (rounding); the norm keeps only R
+  size_t gscr_elems = 0;  // global scratch for spilled leaf buffers (elements of the compute type)
+  size_t off_gscr = 0;
   int N = 0;
   int dtype = TT_F64;
   int nsm = 152;
@@ -1060,69 +1101,72 @@ static int device_sm_count() {
   return n;
 }
 
+// largest shared-memory footprint of the kernels that core n runs with tile Tt
+template <typename T>
+static size_t core_smem(const RoundPlan &pl, int n, int Tt, bool spill, bool sweep1_only, size_t *gstride) {
+  const CorePlan &c = pl.core[n];
+  const int N = pl.N, CC = 8;
+  size_t mx = 0, g = 0;
+  auto acc = [&](size_t bytes, size_t gs) {
+    mx = std::max(mx, bytes);
+    g = std::max(g, gs);
+  };
+  if (n >= 1) {
+    const SmemS1<T> a = smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC, spill);
+    acc(a.bytes, a.gstride);
+    if (!sweep1_only) {
+      if (n < N - 1) {
+        const SmemS2<T> b = smem_s2<T>(0, c.R0, c.K1, c.K0, Tt, 1, CC, spill);
+        const SmemOut<T> o = smem_out<T>(c.K1, c.K0, Tt, spill);
+        acc(b.bytes, b.gstride);
+        acc(o.bytes, o.gstride);
+      } else {
+        const SmemS2<T> b = smem_s2<T>(2, c.R0, c.K1, c.K0, Tt, 1, CC, spill);
+        acc(b.bytes, b.gstride);
+      }
+    }
+  } else if (!sweep1_only) {
+    const SmemS2<T> b = smem_s2<T>(1, 1, c.K1, 1, Tt, c.R1, CC, spill);
+    const SmemOut<T> o = smem_out<T>(c.K1, 1, Tt, spill);
+    acc(b.bytes, b.gstride);
+    acc(o.bytes, o.gstride);
+  }
+  if (gstride) *gstride = g;
+  return mx;
+}
+
+// Tile height (slices per tile) per core: the largest that fits, then shrunk while that
+// lets two leaf CTAs share an SM.  Cores whose buffers do not fit even with one slice per
+// tile move their running factor and carried block to a per-leaf global scratch.
 template <typename T>
 static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
   const int N = pl.N;
+  pl.gscr_elems = 0;
   for (int n = 0; n < N; ++n) {
     CorePlan &c = pl.core[n];
-    if (sweep1_only) {
-      // the orthonormalization norm runs the right-to-left sweep only
-      if (n == 0) continue;
-      int best1 = 0;
-      for (int Tt = 1; Tt <= 64 && Tt <= (c.I + c.P - 1) / c.P; ++Tt) {
-        if (Tt * c.K1 > 512 && Tt > 1) break;
-        if (smem_s1<T>(c.R0, c.K1, c.R1, Tt, 8).bytes > kSmemBudget) break;
-        best1 = Tt;
-        if (smem_s1<T>(c.R0, c.K1, c.R1, Tt, 8).bytes > kSmemPair && best1 > 1) break;
-      }
-      if (best1 == 0) return false;
-      c.Tt = best1;
-      continue;
-    }
+    if (sweep1_only && n == 0) continue;
     const int64_t per_leaf = (c.I + c.P - 1) / c.P;
-    int best = 0;
-    const int CC = 8;
     const int maxT = n == 0 ? 512 : 64;
-    for (int Tt = 1; Tt <= maxT && Tt <= per_leaf; ++Tt) {
-      bool ok = true;
-      if (n >= 1) {
-        const int rows = Tt * c.K1;
-        if (rows > 512 && Tt > 1) break;
-        ok = ok && smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC).bytes <= kSmemBudget;
-        if (n < N - 1) {
-          ok = ok && smem_s2<T>(0, c.R0, c.K1, c.K0, Tt, 1, CC).bytes <= kSmemBudget;
-          ok = ok && smem_out<T>(c.K1, c.K0, Tt).bytes <= kSmemBudget;
-        } else {
-          ok = ok && smem_s2<T>(2, c.R0, c.K1, c.K0, Tt, 1, CC).bytes <= kSmemBudget;
-        }
-      } else {
-        ok = ok && smem_s2<T>(1, 1, c.K1, 1, Tt, c.R1, CC).bytes <= kSmemBudget;
-        ok = ok && smem_out<T>(c.K1, 1, Tt).bytes <= kSmemBudget;
+    int best = 0;
+    for (int sp = 0; sp < 2 && best == 0; ++sp) {
+      c.spill = sp == 1;
+      for (int Tt = 1; Tt <= maxT && Tt <= per_leaf; ++Tt) {
+        if (n >= 1 && Tt * c.K1 > 512 && Tt > 1) break;
+        if (core_smem<T>(pl, n, Tt, c.spill, sweep1_only, nullptr) > kSmemBudget) break;
+        best = Tt;
       }
-      if (!ok) break;
-      best = Tt;
     }
     if (best == 0) return false;
     c.Tt = best;
-    // largest tile whose footprint still lets two leaf CTAs share an SM
     for (int Tt = best; Tt >= 1; --Tt) {
-      size_t mx = 0;
-      if (n >= 1) {
-        mx = smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC).bytes;
-        if (n < N - 1) {
-          mx = std::max(mx, smem_s2<T>(0, c.R0, c.K1, c.K0, Tt, 1, CC).bytes);
-          mx = std::max(mx, smem_out<T>(c.K1, c.K0, Tt).bytes);
-        } else {
-          mx = std::max(mx, smem_s2<T>(2, c.R0, c.K1, c.K0, Tt, 1, CC).bytes);
-        }
-      } else {
-        mx = std::max(smem_s2<T>(1, 1, c.K1, 1, Tt, c.R1, CC).bytes, smem_out<T>(c.K1, 1, Tt).bytes);
-      }
-      if (mx <= kSmemPair) {
+      if (core_smem<T>(pl, n, Tt, c.spill, sweep1_only, nullptr) <= kSmemPair) {
         c.Tt = Tt;
         break;
       }
     }
+    size_t g = 0;
+    core_smem<T>(pl, n, c.Tt, c.spill, sweep1_only, &g);
+    pl.gscr_elems = std::max(pl.gscr_elems, g * (size_t)c.P);
   }
   return true;
 }
@@ -1161,7 +1205,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
   for (int n = 0; n + 1 < N && !sweep1_only; ++n)
     if (smem_svd(pl.core[n].K1, false) > kSmemBudget) return TT_ERR_UNSUPPORTED;
   for (int n = 1; n < N; ++n)
-    if (smem_tree(pl.core[n].R0, 1).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
+    if (smem_tree(pl.core[n].R0, pl.core[n].R0).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
   // workspace layout
   Carve w;
   pl.off_L = w.take(sizeof(int) * (N + 1), 256);
@@ -1177,7 +1221,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
     if (n >= 1 && pl.keep_q) {
       c.refl_off = w.take(sizeof(T) * (size_t)c.I * c.K1 * c.R0, 256);
       c.tau_off = w.take(sizeof(T) * (size_t)c.I * c.R0, 256);
-      const SmemTree st = smem_tree(c.R0, 1);
+      const SmemTree st = smem_tree(c.R0, c.R0);
       c.slot_off = w.take(sizeof(double) * c.tree.nslots * ((size_t)c.R0 * c.R0 + (size_t)st.nchunk * c.R0), 256);
     }
     if (n < N - 1) {
@@ -1196,6 +1240,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
     pl.off_tau2 = w.take(sizeof(T) * max_tau2, 256);
   }
   pl.off_part = w.take(sizeof(double) * 4096, 256);
+  pl.off_gscr = w.take(sizeof(T) * std::max<size_t>(pl.gscr_elems, 1), 256);
   pl.total = w.off;
   return TT_OK;
 }
@@ -1233,7 +1278,7 @@ static int set_smem(K kernel, size_t bytes) {
 // level-by-level tree factorization of the leaf R's in Rbuf level 0; root ends at level nlev
 static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, double *Rbase, double *slots,
                        int B, cudaStream_t st) {
-  const SmemTree sm = smem_tree(b, 1);
+  const SmemTree sm = smem_tree(b, b);  // same chunking as the apply (at most b columns)
   int r = set_smem(k_tree_factor, sm.bytes);
   if (r) return r;
   for (int l = 0; l < tr.nlev; ++l) {
@@ -1271,7 +1316,7 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
 static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, int ncol, const int *ncol_dyn,
                       int cmax, double *Cbase, const double *slots, int B, cudaStream_t st) {
   const SmemTree sm = smem_tree(b, cmax);
-  const SmemTree smf = smem_tree(b, 1);  // the slots hold the factorization's chunking
+  const SmemTree smf = smem_tree(b, b);  // the slots hold the factorization's chunking
   SmemTree use = sm;
   use.MT = smf.MT;
   use.nchunk = smf.nchunk;
@@ -1330,8 +1375,10 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
   const double *Pm = nullptr;  // root R of the previous core (device), K_{n+1} x R_{n+1}
   for (int n = N - 1; n >= 1; --n) {
     const CorePlan &c = pl.core[n];
-    const SmemS1<T> m = smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8);
+    const SmemS1<T> m = smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8, c.spill);
     S1Args<S, T> a{};
+    a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
+    a.gstride = m.gstride;
     a.X = reinterpret_cast<const S *>(x->cores[n]);
     a.g = Geom{c.I, c.P, c.Tt};
     a.b = c.R0;
@@ -1372,9 +1419,12 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
   return TT_OK;
 }
 
+// Queues a whole rounding on st.  Sync mode (ranks_dev == nullptr): waits and returns the
+// ranks in out->R.  Async mode: copies the ranks (N+1 ints) to ranks_dev and the status
+// word to status_dev, device side, and returns without a host synchronization.
 template <typename S, typename T>
 static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_tensor *out, unsigned char *ws,
-                     cudaStream_t st) {
+                     cudaStream_t st, int *ranks_dev = nullptr, int *status_dev = nullptr) {
   const int N = pl.N;
   const int B = pl.bmax;
   int *dL = reinterpret_cast<int *>(ws + pl.off_L);
@@ -1408,8 +1458,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     }
     {
       const int mode = n == 0 ? 1 : 0;
-      const SmemS2<T> m = smem_s2<T>(mode, n == 0 ? 1 : c.R0, K1, n == 0 ? 1 : c.K0, c.Tt, c.R1, 8);
+      const SmemS2<T> m = smem_s2<T>(mode, n == 0 ? 1 : c.R0, K1, n == 0 ? 1 : c.K0, c.Tt, c.R1, 8, c.spill);
       S2Args<S, T> a{};
+      a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
+      a.gstride = m.gstride;
       a.mode = mode;
       a.g = Geom{c.I, c.P, c.Tt};
       if (n >= 1) {
@@ -1485,8 +1537,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     r = tree_apply(c.tree, K1, c.I, 1, n == 0 ? nullptr : dL + n, 0, dL + n + 1, K1, C2, slots2, B, st);
     if (r) return r;
     {
-      const SmemOut<T> m = smem_out<T>(K1, n == 0 ? 1 : c.K0, c.Tt);
+      const SmemOut<T> m = smem_out<T>(K1, n == 0 ? 1 : c.K0, c.Tt, c.spill);
       OutArgs<S, T> a{};
+      a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
+      a.gstride = m.gstride;
       a.g = Geom{c.I, c.P, c.Tt};
       a.vrefl = refl2;
       a.vtau = tau2;
@@ -1519,8 +1573,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     r = tree_apply(c.tree, c.R0, c.I, c.K1, nullptr, 0, dL + N - 1, c.K0, C1,
                    reinterpret_cast<double *>(ws + c.slot_off), B, st);
     if (r) return r;
-    const SmemS2<T> m = smem_s2<T>(2, c.R0, 1, c.K0, c.Tt, 1, 8);
+    const SmemS2<T> m = smem_s2<T>(2, c.R0, 1, c.K0, c.Tt, 1, 8, c.spill);
     S2Args<S, T> a{};
+    a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
+    a.gstride = m.gstride;
     a.mode = 2;
     a.g = Geom{c.I, c.P, c.Tt};
     a.qrefl = reinterpret_cast<const T *>(ws + c.refl_off);
@@ -1552,6 +1608,11 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     }
     TT_CUDA(cudaGetLastError());
   }
+  if (ranks_dev) {
+    TT_CUDA(cudaMemcpyAsync(ranks_dev, dL, sizeof(int) * (N + 1), cudaMemcpyDeviceToDevice, st));
+    TT_CUDA(cudaMemcpyAsync(status_dev, dstatus, sizeof(int), cudaMemcpyDeviceToDevice, st));
+    return TT_OK;
+  }
   // ranks and status back to the host
   std::vector<int> L(N + 1);
   int status[4];
@@ -1563,10 +1624,22 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   return TT_OK;
 }
 
-int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+__global__ void k_ranks_one(int *ranks, int *status) {
+  if (threadIdx.x < 2) ranks[threadIdx.x] = 1;
+  if (threadIdx.x == 0) status[0] = 0;
+}
+
+int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes,
+                  cudaStream_t st, int *ranks_dev, int *status_dev) {
   if (x->N == 1) {
     const size_t es = x->dtype == TT_F64 ? 8 : 4;
     TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDeviceToDevice, st));
+    if (ranks_dev) {
+      TraceScope ts_(TT_K_MISC, st);
+      k_ranks_one<<<1, 32, 0, st>>>(ranks_dev, status_dev);
+      TT_CUDA(cudaGetLastError());
+      return TT_OK;
+    }
     TT_CUDA(cudaStreamSynchronize(st));
     out->R[0] = out->R[1] = 1;
     return TT_OK;
@@ -1577,10 +1650,14 @@ int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws
   if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
   unsigned char *w = reinterpret_cast<unsigned char *>(ws);
   switch (prec) {
-    case TT_PREC_FP64: return run_round<double, double>(pl, x, eps, out, w, st);
-    case TT_PREC_FP32X2: return run_round<float, df32>(pl, x, eps, out, w, st);
-    default: return run_round<float, float>(pl, x, eps, out, w, st);
+    case TT_PREC_FP64: return run_round<double, double>(pl, x, eps, out, w, st, ranks_dev, status_dev);
+    case TT_PREC_FP32X2: return run_round<float, df32>(pl, x, eps, out, w, st, ranks_dev, status_dev);
+    default: return run_round<float, float>(pl, x, eps, out, w, st, ranks_dev, status_dev);
   }
+}
+
+int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+  return round_enqueue(x, eps, prec, out, ws, ws_bytes, st, nullptr, nullptr);
 }
 
 static int norm_prec(const tt_tensor *x) { return x->dtype == TT_F64 ? TT_PREC_FP64 : TT_PREC_FP32X2; }
