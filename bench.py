@@ -44,6 +44,9 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--modes", type=int, default=I_MODE, help="mode size I_n (default: the full 65536)")
+    p.add_argument("--variants", type=int, default=1,
+                   help="1: also time the mixed-precision and batched forms (N=1 only), 0: skip")
+    p.add_argument("--batch", type=int, default=64, help="tensors of the batched recipe timed in the variants")
     return p.parse_args()
 
 
@@ -192,6 +195,100 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------
+# variants: the mixed-precision and batched forms beside plain FP64, same box, same run
+# --------------------------------------------------------------------------------------
+
+def _time(fn, reps=2):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) / reps
+
+
+def run_variants(args):
+    """Decaying-spectrum workload (N=50, I_n=16384, formal ranks 64, eps=1e-5) in fp64,
+    fp32x2 and fp32, and the first `args.batch` tensors of the 512-tensor batched recipe
+    (N in 4..20, I_n in 64..4096, ranks 2r with r in 4..48, eps=1e-6): a loop of FP64
+    roundings against one graph-captured batch in fp32x2 and fp32."""
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+    import ttgen
+
+    out = {}
+
+    def neg_first(x):
+        c = [t.clone() for t in x.cores]
+        c[0] = -c[0]
+        return ttgb.DeviceTT(list(x.I), list(x.R), c)
+
+    def as64(x):
+        return ttgb.DeviceTT(list(x.I), list(x.R), [c.double() for c in x.cores])
+
+    # ---- mixed precision on the decaying-spectrum workload
+    terms = ttgen.decaying_terms(50, 16384, ttgen.BASE_SEED + 3)
+    X = ttgb.from_host(terms[0].I, terms[0].R, terms[0].cores)
+    for T in terms[1:]:
+        X = ttgb.tt_add(X, ttgb.from_host(T.I, T.R, T.cores))
+    del terms
+    X32 = ttgb.DeviceTT(list(X.I), list(X.R), [c.float() for c in X.cores])
+    res = {}
+    y64 = ttgb.tt_round(X, 1e-5)
+    t64 = _time(lambda: ttgb.tt_round(X, 1e-5))
+    res["fp64"] = {"tt_rounds_per_s": 1.0 / t64, "ms": t64 * 1e3, "ranks_max": max(y64.R)}
+    n64 = ttgb.tt_norm(y64)
+    for prec in ("fp32x2", "fp32"):
+        ttgb._ws_cache.clear()
+        torch.cuda.empty_cache()
+        y = ttgb.tt_round(X32, 1e-5, precision=prec)
+        t = _time(lambda: ttgb.tt_round(X32, 1e-5, precision=prec))
+        err = ttgb.tt_norm(ttgb.tt_add(as64(y), neg_first(y64))) / n64
+        res[prec] = {"tt_rounds_per_s": 1.0 / t, "ms": t * 1e3, "rel_err_vs_fp64": err, "ranks_equal": y.R == y64.R,
+                     "speedup_vs_fp64": t64 / t}
+    out["decaying_N50_I16384_eps1e-5"] = res
+    del X, X32, y64
+    ttgb._ws_cache.clear()
+    torch.cuda.empty_cache()
+
+    # ---- batched recipe: FP64 loop vs one graph-captured batch
+    shapes = ttgen.batched_shapes()[: args.batch]
+    X64 = []
+    for t, (I, r) in enumerate(shapes):
+        (I_, R, Y), (_, _, Yp) = ttgen.device_perturbed_pair(I, r, ttgen.BASE_SEED + 4 + 97 * t)
+        X64.append(ttgb.tt_add(ttgb.DeviceTT(I_, R, Y), ttgb.DeviceTT(I_, R, Yp)))
+    torch.cuda.synchronize()
+    X32 = [ttgb.DeviceTT(x.I, x.R, [c.float() for c in x.cores]) for x in X64]
+    eps = [1e-6] * len(X64)
+    res = {"tensors": len(X64), "input_gb_fp32": sum(x.nbytes() for x in X32) / 1e9}
+    t_loop = _time(lambda: [ttgb.tt_round(x, 1e-6) for x in X64], reps=1)
+    res["fp64_loop"] = {"tts_per_s": len(X64) / t_loop, "ms": t_loop * 1e3}
+    ref = [ttgb.tt_round(x, 1e-6) for x in X64]
+    for prec in ("fp32x2", "fp32"):
+        b = ttgb.Batch(X32, eps, prec)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            b.enqueue(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.enqueue(s)
+        t = _time(g.replay, reps=1)
+        got = b.outputs()
+        res[prec + "_graph"] = {"tts_per_s": len(X64) / t, "ms": t * 1e3, "speedup_vs_fp64_loop": t_loop / t,
+                                "ranks_equal": all(a.R == o.R for a, o in zip(ref, got))}
+        del b, g
+        torch.cuda.empty_cache()
+    out["batched_first%d" % len(X64)] = res
+    return out
+
+
+# --------------------------------------------------------------------------------------
 # this library
 # --------------------------------------------------------------------------------------
 
@@ -301,6 +398,13 @@ def run_ours(args):
                "sample": f"oracle tt_round of the same construction with I_n={I_s} ({t_cpu:.1f} s), "
                          f"scaled by {I_s}/{args.modes} (cost is linear in I_n)"}
 
+    variants = None
+    if world == 1 and args.variants:
+        del X, dX, hX, hOut
+        ttgb._ws_cache.clear()
+        torch.cuda.empty_cache()
+        variants = run_variants(args)
+
     alg_bytes = 2 * in_bytes + out_bytes  # two reads of the input cores, one write of the output
     line = {
         "metric": METRIC, "value": rounds_per_s, "unit": "TT-rounds/s", "n_gpus": world, "steps": args.steps,
@@ -321,6 +425,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,
         "clocks": clk,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -258,3 +258,30 @@ def batched_shapes(count: int = 512, seed: int = BASE_SEED + 4):
 def batched_member(t: int, count: int = 512, seed: int = BASE_SEED + 4):
     Is, r = batched_shapes(count, seed)[t]
     return perturbed_pair(Is, r, seed + 17, stream=t), 1e-6
+
+
+def device_random_tt(I: Sequence[int], R: Sequence[int], seed: int, device="cuda"):
+    """Random TT cores drawn on the GPU with torch's seeded Philox generator, for timing
+    runs whose inputs are too large to draw on the host in reasonable time.  Entries are
+    N(0,1)/sqrt(I_n R_{n-1}) like random_tt, but the values differ from the host
+    generator's, so these inputs are never used where the oracle is compared.
+    Returns (I, R, cores) with cores as flat float64 CUDA tensors."""
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    I = [int(x) for x in I]
+    R = [int(x) for x in R]
+    cores = [torch.randn(R[n] * I[n] * R[n + 1], generator=gen, device=device, dtype=torch.float64)
+             / float(np.sqrt(I[n] * R[n])) for n in range(len(I))]
+    return I, R, cores
+
+
+def device_perturbed_pair(I: Sequence[int], r: int, seed: int, device="cuda"):
+    """Device-drawn (Y, Y') of the perturbed-pair recipe (see perturbed_pair)."""
+    N = len(I)
+    R = uniform_ranks(N, r)
+    _, _, Y = device_random_tt(I, R, seed, device)
+    _, _, Z = device_random_tt(I, R, seed + 1000, device)
+    Yp = [(0.5 if n == 0 else 1.0) * Y[n] + 1e-9 * Z[n] for n in range(N)]
+    return (list(I), R, Y), (list(I), R, Yp)
