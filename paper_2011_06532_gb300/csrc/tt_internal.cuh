@@ -211,7 +211,10 @@ struct Scratch {
 
 // H = I - tau u u^T with u = [1; v], v_r = V[r * ldv] for r in [r0, M), applied to the
 // stacked matrix [p (nc entries); X rows r0..M-1 (nc entries each, row stride ldx)].
-// All threads of the CTA must call it with identical arguments; nc <= NT.
+// Thread t owns column c = t mod nc of row group g = t / nc (G = NT / nc groups, so short
+// trailing blocks still spread over the whole CTA); the partial dot products are summed by
+// a tree in shared memory, then w_c = tau (p_c + v^T X(:, c)) and X -= v w^T over the dense
+// block.  All threads of the CTA must call it with identical arguments; nc <= NT.
 template <typename T>
 __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, int ldx, int nc, Scratch<T> s) {
   if (nc <= 0) return;
@@ -219,13 +222,12 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
   const int nrow = M - r0;
   int G = NT / nc;
   if (G > nrow) G = nrow > 0 ? nrow : 1;
-  // partial dot products v^T X(:, c) over row groups
   if (t < G * nc) {
     const int g = t / nc, c = t - g * nc;
     if constexpr (is_df<T>::value) {
-      float sh = 0.f, sc = 0.f;
-      for (int r = r0 + g; r < M; r += G) df_dot_acc(sh, sc, V[(size_t)r * ldv], X[(size_t)r * ldx + c]);
-      s.red[g * nc + c] = df_finish(sh, sc);
+      float sh = 0.f, sl = 0.f;
+      for (int r = r0 + g; r < M; r += G) df_dot_acc(sh, sl, V[(size_t)r * ldv], X[(size_t)r * ldx + c]);
+      s.red[g * nc + c] = df_finish(sh, sl);
     } else {
       T acc = T(0);
       for (int r = r0 + g; r < M; r += G) acc += V[(size_t)r * ldv] * X[(size_t)r * ldx + c];
@@ -248,18 +250,19 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
   if (nrow > 0) {
     // dense walk over the nrow x nc block without per-element division
     const int dq = NT / nc, dr = NT - dq * nc;
-    int r = t / nc, c = t - (t / nc) * nc;
+    int r = t / nc, cc = t - (t / nc) * nc;
     for (; r < nrow;) {
+      const size_t rr = (size_t)(r0 + r);
       if constexpr (is_df<T>::value) {
-        T &x = X[(size_t)(r0 + r) * ldx + c];
-        x = df_sub_prod(x, V[(size_t)(r0 + r) * ldv], s.wbuf[c]);
+        T &x = X[rr * ldx + cc];
+        x = df_sub_prod(x, V[rr * ldv], s.wbuf[cc]);
       } else {
-        X[(size_t)(r0 + r) * ldx + c] -= V[(size_t)(r0 + r) * ldv] * s.wbuf[c];
+        X[rr * ldx + cc] -= V[rr * ldv] * s.wbuf[cc];
       }
       r += dq;
-      c += dr;
-      if (c >= nc) {
-        c -= nc;
+      cc += dr;
+      if (cc >= nc) {
+        cc -= nc;
         ++r;
       }
     }

@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
   const int b = a.b, rho = a.rho, cin = a.cin, ldt = a.ldt;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
   const bool push = a.Pm != nullptr;
-  // FP64 reads the pushed factor straight from L1/L2 (no conversion, no shared copy);
-  // other compute types stage a converted copy
+  // FP64 reads the pushed factor through L1 (no conversion needed, and the shared memory
+  // it would take lets more leaf CTAs share an SM); other compute types stage a converted copy
   constexpr bool stage = !std::is_same<T, double>::value;
   if (push && stage)
     for (int idx = t; idx < rho * cin; idx += NT) Ps[idx] = (T)a.Pm[idx];
@@ -205,19 +205,30 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
           Xs[idx] = T(a.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem]);
         }
         __syncthreads();
-        for (int idx = t; idx < M * b; idx += NT) {
-          const int r = idx / b, col = idx - r * b;
-          const int sl = r / rho, kr = r - sl * rho;
-          T acc = tile[r * ldt + col];
-          const int cstart = max(kr, c0);
-          if constexpr (stage) {
-            for (int c = cstart; c < c0 + cc_n; ++c) acc += Ps[kr * cin + c] * Xs[((c - c0) * nt + sl) * b + col];
-          } else {
-            const double *pr = a.Pm + (size_t)kr * cin;
-            for (int c = cstart; c < c0 + cc_n; ++c) acc += T(__ldg(pr + c)) * Xs[((c - c0) * nt + sl) * b + col];
+        // two copies of the loop so that the staged factor is addressed as shared memory
+        // whenever it lives there
+        auto push_tile = [&](const T *P) {
+          for (int idx = t; idx < M * b; idx += NT) {
+            const int r = idx / b, col = idx - r * b;
+            const int sl = r / rho, kr = r - sl * rho;
+            T acc = tile[r * ldt + col];
+            const int cstart = max(kr, c0);
+            if constexpr (is_df<T>::value) {
+              float ah = acc.hi, al = acc.lo;
+              for (int c = cstart; c < c0 + cc_n; ++c) df_dot_acc(ah, al, P[kr * cin + c], Xs[((c - c0) * nt + sl) * b + col]);
+              acc = df_finish(ah, al);
+            } else {
+              for (int c = cstart; c < c0 + cc_n; ++c) acc += P[kr * cin + c] * Xs[((c - c0) * nt + sl) * b + col];
+            }
+            tile[r * ldt + col] = acc;
           }
-          tile[r * ldt + col] = acc;
-        }
+        };
+        if constexpr (!stage)
+          push_tile(reinterpret_cast<const T *>(a.Pm));
+        else if (a.oPs >= 0)
+          push_tile(sm<T>(smem, a.oPs));
+        else
+          push_tile(Ps);
       }
     }
     __syncthreads();
