@@ -282,10 +282,102 @@ def run_variants(args):
         got = b.outputs()
         res[prec + "_graph"] = {"tts_per_s": len(X64) / t, "ms": t * 1e3, "speedup_vs_fp64_loop": t_loop / t,
                                 "ranks_equal": all(a.R == o.R for a, o in zip(ref, got))}
+        if prec != "fp32x2":
+            del b, g
+            torch.cuda.empty_cache()
+            continue
+        # the same batch after tuning its leaf/tile policy on the GPU
+        t0 = time.perf_counter()
+        b.autotune()
+        tune_s = time.perf_counter() - t0
+        with torch.cuda.stream(s):
+            b.enqueue(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.enqueue(s)
+        t = _time(g.replay, reps=1)
+        got = b.outputs()
+        caps = sorted({int(ln.split()[7]) for ln in ttgb.tune_export().splitlines()
+                       if ln and not ln.startswith("#") and int(ln.split()[7]) < int(ln.split()[2])})
+        res[prec + "_graph_tuned"] = {"tts_per_s": len(X64) / t, "ms": t * 1e3, "speedup_vs_fp64_loop": t_loop / t,
+                                      "ranks_equal": all(a.R == o.R for a, o in zip(ref, got)), "tuning_s": tune_s,
+                                      "leaf_cap": caps[0] if caps else None}
         del b, g
         torch.cuda.empty_cache()
+    ttgb.tune_clear()
     out["batched_first%d" % len(X64)] = res
+    del X64, X32, ref
+    torch.cuda.empty_cache()
+    out["hadamard_pipeline"] = run_pipeline(args)
     return out
+
+
+def run_pipeline(args):
+    """Hadamard pipeline (N=30, I_n=1024): Z = A o B, Y = round(Z, 1e-6), <Y, Z>, ||Y||.
+    Pair 0 (ranks 8 x 8 -> 64) in FP64 and fp32x2; then every pair of the 64-pair recipe
+    whose product rank is within the supported maximum, with the roundings as one batch."""
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+    import ttgen
+
+    res = {}
+
+    def neg_first(x):
+        c = [t.clone() for t in x.cores]
+        c[0] = -c[0]
+        return ttgb.DeviceTT(list(x.I), list(x.R), c)
+
+    A, B = ttgen.hadamard_pair(0)
+    runs = {}
+    for prec, dt in (("fp64", torch.float64), ("fp32x2", torch.float32)):
+        dA = ttgb.from_host(A.I, A.R, A.cores, dtype=dt)
+        dB = ttgb.from_host(B.I, B.R, B.cores, dtype=dt)
+
+        def step():
+            Z = ttgb.tt_hadamard(dA, dB)
+            Y = ttgb.tt_round(Z, 1e-6, precision=prec)
+            return Y, ttgb.tt_dot(Y, Z), ttgb.tt_norm(Y)
+
+        out = step()
+        t = _time(step, reps=2)
+        runs[prec] = out
+        res[prec] = {"ms": t * 1e3, "pipelines_per_s": 1.0 / t, "ranks_max": max(out[0].R)}
+    (y64, d64, n64), (y32, d32, n32) = runs["fp64"], runs["fp32x2"]
+    y32d = ttgb.DeviceTT(list(y32.I), list(y32.R), [c.double() for c in y32.cores])
+    res["fp32x2"].update({
+        "speedup_vs_fp64": res["fp64"]["ms"] / res["fp32x2"]["ms"],
+        "rel_err_Y_vs_fp64": ttgb.tt_norm(ttgb.tt_add(y32d, neg_first(y64))) / n64,
+        "rel_err_dot_vs_fp64": abs(d32 - d64) / abs(d64), "ranks_equal": y32.R == y64.R})
+    del runs, y64, y32, y32d
+    torch.cuda.empty_cache()
+    # the batch of supported pairs (inputs drawn on the device; timing only)
+    shapes = ttgen.hadamard_pair_shapes()
+    pairs = [p for p, (ra, rb) in enumerate(shapes) if ra * rb <= 96]
+    N, I = 30, 1024
+    Zs = []
+    for p in pairs:
+        ra, rb = shapes[p]
+        _, Ra, ca = ttgen.device_random_tt([I] * N, ttgen.uniform_ranks(N, ra), ttgen.BASE_SEED + 5 + 2 * p)
+        _, Rb, cb = ttgen.device_random_tt([I] * N, ttgen.uniform_ranks(N, rb), ttgen.BASE_SEED + 6 + 2 * p)
+        a = ttgb.DeviceTT([I] * N, Ra, [c.float() for c in ca])
+        b = ttgb.DeviceTT([I] * N, Rb, [c.float() for c in cb])
+        Zs.append((a, b))
+        del ca, cb
+
+    def batch_step():
+        Z = [ttgb.tt_hadamard(a, b) for a, b in Zs]
+        Y = ttgb.Batch(Z, [1e-6] * len(Z), "fp32x2").run()
+        return [(ttgb.tt_dot(y, z), ttgb.tt_norm(y)) for y, z in zip(Y, Z)]
+
+    t = _time(batch_step, reps=1)
+    res["batch_fp32x2"] = {"pairs": len(pairs), "of_recipe_pairs": len(shapes), "ms": t * 1e3,
+                           "pipelines_per_s": len(pairs) / t,
+                           "note": "pairs whose product rank exceeds 96 are outside the supported range"}
+    del Zs
+    torch.cuda.empty_cache()
+    return res
 
 
 # --------------------------------------------------------------------------------------

@@ -114,9 +114,12 @@ int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void
  * Batched rounding of `count` independent tensors (each as in tt_round, eps[k]
  * per tensor, one precision for all).  The batch is spread over up to
  * TT_BATCH_SLOTS internal CUDA streams forked from `stream` and joined back
- * into it; tensor k runs on slot k mod TT_BATCH_SLOTS, in order, and each slot
- * owns one region of the workspace.  The library creates those streams and
- * their events once per device on first use and keeps them until exit.
+ * into it, each slot owning one region of the workspace.  Tensors are assigned
+ * largest first (work ~ sum_n R_{n-1} I_n R_n max(R_{n-1}, R_n)), each to the
+ * slot with the least work so far; ties go to the lowest slot.  The library
+ * creates those streams and their events once per device on first use and
+ * keeps them until exit.  Members are planned in the batch context of the
+ * tile table (see tt_autotune_batched).
  */
 #define TT_BATCH_SLOTS 16
 
@@ -138,6 +141,76 @@ int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int 
 int tt_round_batched_async(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
                            int32_t *ranks_dev, int32_t *status_dev, void *workspace, size_t workspace_bytes,
                            void *stream);
+
+/*
+ * Tile autotuning.  Each core of a rounding is split into P leaves (CTAs) over
+ * its I_n slices (the leaves of the TSQR tree, Sec. 4.1), each leaf walking its
+ * slab in tiles of Tt slices.  Without tuning the library takes P = 2 leaves per
+ * SM (at most I_n) and the largest tile that lets two leaves share an SM.  The
+ * tuner times complete roundings of the given tensor(s) on the GPU and records,
+ * per core class (precision, context, I_n, R_{n-1}, R_n and the ranks after the
+ * orthogonalization sweep), the fastest (P, Tt) it tried, in a table that every
+ * later plan of the process consults (including tt_norm's, which shares the
+ * orthogonalization sweep).  A tuned plan computes the same rounding with a
+ * different reduction tree, so results agree with the untuned ones to rounding
+ * error, not bit for bit; ranks are chosen identically unless a singular value
+ * sits within rounding error of the threshold.
+ *
+ * Workspace sizes depend on the table: query them after tuning (or importing),
+ * and re-query whenever tt_tune_generation() has changed.  A call given a
+ * workspace sized under an older table returns TT_ERR_WORKSPACE.
+ */
+
+/* Workspace covering every candidate plan of tt_autotune for x. */
+int tt_autotune_workspace_size(const tt_tensor *x, int precision, size_t *bytes);
+
+/*
+ * Tunes the core classes of x for a single rounding: coordinate descent over
+ * the classes, largest first, over P in {P_default, SMs/2, SMs, 2 SMs, 3 SMs,
+ * 4 SMs} (clamped to [1, min(I_n, 1024)]) and Tt in {T_default, T_default/2,
+ * largest that fits}; each candidate is timed (best of two) by complete
+ * roundings of x into out, and kept if it is 2 % faster than the incumbent.
+ * On return `out` holds a valid rounding of x (as from tt_round) and the table
+ * holds the winners.  Same argument rules and errors as tt_round, plus
+ * TT_ERR_WORKSPACE below tt_autotune_workspace_size.  Synchronizes `stream`.
+ */
+int tt_autotune(const tt_tensor *x, double eps, int precision, tt_tensor *out, void *workspace,
+                size_t workspace_bytes, void *stream);
+
+/* Workspace covering every candidate policy of tt_autotune_batched. */
+int tt_autotune_batched_workspace_size(int32_t count, const tt_tensor *xs, int precision, size_t *bytes);
+
+/*
+ * Tunes a batch: one policy for all members, P = min(c SMs, I_n) with c in
+ * {4, 2, 1, 1/2, 1/4, 1/8, 1/16} and Tt either T_default or the largest that
+ * fits.  Each leaf cap is timed with T_default by one complete batched rounding
+ * into outs (after one untimed rounding with the current plans), then the other
+ * tile rule at the best cap (kept if 2 % faster); the winner is recorded for
+ * every member class in the batch context.  Arguments and errors as
+ * tt_round_batched.
+ */
+int tt_autotune_batched(int32_t count, const tt_tensor *xs, const double *eps, int precision, tt_tensor *outs,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * The table as text, one entry per line "prec ctx I R0 R1 K0 K1 P Tt" (ctx 0 =
+ * single rounding, 1 = batch member; P or Tt 0 = default) after one comment
+ * line.  *length = bytes needed including the terminating NUL; buf may be NULL
+ * to query it; TT_ERR_WORKSPACE if capacity is short.
+ */
+int tt_tune_export(char *buf, size_t capacity, size_t *length);
+
+/* Adds the entries of a text in tt_tune_export's format (lines starting with '#'
+ * and blank lines ignored).  TT_ERR_INVALID_ARG, with the table unchanged, if any
+ * line is malformed or out of range (prec 1..3, ctx 0..1, I >= 1, 1 <= K0 <= R0
+ * <= TT_MAX_RANK, 1 <= K1 <= R1 <= TT_MAX_RANK, 0 <= P <= 1024, Tt >= 0). */
+int tt_tune_import(const char *text);
+
+/* Empties the table (plans go back to the defaults). */
+int tt_tune_clear(void);
+
+/* Counter bumped by every change of the table. */
+uint64_t tt_tune_generation(void);
 
 /*
  * Summation (Sec. 3.2.1): Z = A + B.  Interior slices are block diagonal

@@ -138,6 +138,50 @@ def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tens
     return DeviceTT(list(x.I), R, cores)
 
 
+def autotune(x: DeviceTT, eps: float, precision: str = "default", stream=None) -> DeviceTT:
+    """Tunes the leaves and tile rows of x's core classes for single roundings (timing
+    complete roundings on the GPU, see tt_autotune) and returns the last rounding of x.
+    Later plans of this process use the recorded choices."""
+    _validate(x)
+    lib = _native.load()
+    dev = x.cores[0].device
+    prec = PRECISIONS[precision]
+    d = _Desc(x.I, x.R, x.cores, x.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_autotune_workspace_size(d.ref, prec, ctypes.byref(n)), "tt_autotune_workspace_size")
+    ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+    out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
+    o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
+    _check(lib.tt_autotune(d.ref, float(eps), prec, o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                           _stream(stream)), "tt_autotune")
+    R = o.ranks()
+    return DeviceTT(list(x.I), R, [out[k][: R[k] * x.I[k] * R[k + 1]] for k in range(x.N)])
+
+
+def tune_export() -> str:
+    """The tile table as text (one "prec ctx I R0 R1 K0 K1 P Tt" line per entry)."""
+    lib = _native.load()
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_tune_export(None, 0, ctypes.byref(n)), "tt_tune_export")
+    buf = ctypes.create_string_buffer(int(n.value))
+    _check(lib.tt_tune_export(buf, ctypes.c_size_t(n.value), ctypes.byref(n)), "tt_tune_export")
+    return buf.value.decode()
+
+
+def tune_import(text: str) -> None:
+    """Adds the entries of a text written by tune_export to the tile table."""
+    _check(_native.load().tt_tune_import(text.encode()), "tt_tune_import")
+
+
+def tune_clear() -> None:
+    """Empties the tile table: plans go back to the built-in choices."""
+    _check(_native.load().tt_tune_clear(), "tt_tune_clear")
+
+
+def tune_generation() -> int:
+    return int(_native.load().tt_tune_generation())
+
+
 class Batch:
     """A prepared batch: descriptors, output buffers and workspace of a list of tensors.
 
@@ -162,10 +206,37 @@ class Batch:
         _check(lib.tt_round_batched_workspace_size(len(xs), self.arr_in, self.prec, ctypes.byref(n)),
                "tt_round_batched_workspace_size")
         self.ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+        self.gen = tune_generation()
         self.ranks_dev = torch.zeros(sum(x.N + 1 for x in xs), dtype=torch.int32, device=dev)
         self.status_dev = torch.zeros(len(xs), dtype=torch.int32, device=dev)
 
+    def _resize(self) -> None:
+        # plans (and so workspace sizes) follow the tile table
+        if self.gen == tune_generation():
+            return
+        n = ctypes.c_size_t(0)
+        _check(_native.load().tt_round_batched_workspace_size(len(self.xs), self.arr_in, self.prec, ctypes.byref(n)),
+               "tt_round_batched_workspace_size")
+        if self.ws.numel() < int(n.value):
+            self.ws = torch.empty(int(n.value), dtype=torch.uint8, device=self.ws.device)
+        self.gen = tune_generation()
+
+    def autotune(self, stream=None) -> None:
+        """Tunes one leaf/tile policy for the members of this batch (tt_autotune_batched);
+        later runs and enqueues of any batch with these member shapes use it."""
+        lib = _native.load()
+        n = ctypes.c_size_t(0)
+        _check(lib.tt_autotune_batched_workspace_size(len(self.xs), self.arr_in, self.prec, ctypes.byref(n)),
+               "tt_autotune_batched_workspace_size")
+        ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=self.ws.device)
+        _check(lib.tt_autotune_batched(len(self.xs), self.arr_in, self.eps, self.prec, self.arr_out,
+                                       ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()), _stream(stream)),
+               "tt_autotune_batched")
+        del ws
+        self._resize()
+
     def run(self, stream=None) -> List[DeviceTT]:
+        self._resize()
         lib = _native.load()
         _check(lib.tt_round_batched(len(self.xs), self.arr_in, self.eps, self.prec, self.arr_out,
                                     ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_size_t(self.ws.numel()),
@@ -177,6 +248,7 @@ class Batch:
         return res
 
     def enqueue(self, stream=None) -> None:
+        self._resize()
         lib = _native.load()
         _check(lib.tt_round_batched_async(len(self.xs), self.arr_in, self.eps, self.prec, self.arr_out,
                                           ctypes.c_void_p(self.ranks_dev.data_ptr()),

@@ -18,7 +18,7 @@ CSRC = os.path.join(_HERE, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libttgb.so")
-SOURCES = ["tt_round.cu", "tt_ops.cu", "tt_api.cu"]
+SOURCES = ["tt_round.cu", "tt_ops.cu", "tt_api.cu", "tt_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -76,6 +76,8 @@ EXPORTS = [
     "tt_round_workspace_size", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard",
     "tt_dot_workspace_size", "tt_dot", "tt_norm_workspace_size", "tt_norm", "tt_status_string",
     "tt_trace", "tt_trace_read", "tt_dot_noalloc", "tt_round_batched_workspace_size", "tt_round_batched_async",
+    "tt_autotune_workspace_size", "tt_autotune", "tt_autotune_batched_workspace_size", "tt_autotune_batched",
+    "tt_tune_export", "tt_tune_import", "tt_tune_clear", "tt_tune_generation",
 ]
 KERNEL_KINDS = ["s1_leaf", "tree_factor", "tree_apply", "s2_leaf", "s2_out", "svd", "add", "hadamard", "dot", "misc"]
 
@@ -107,6 +109,13 @@ def load(path: str | None = None):
         "tt_dot_noalloc": [T, T, dp, vp],
         "tt_norm_workspace_size": [T, sz],
         "tt_norm": [T, dp, vp, ctypes.c_size_t, vp],
+        "tt_autotune_workspace_size": [T, ctypes.c_int, sz],
+        "tt_autotune": [T, ctypes.c_double, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_autotune_batched_workspace_size": [ctypes.c_int32, T, ctypes.c_int, sz],
+        "tt_autotune_batched": [ctypes.c_int32, T, dp, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_tune_export": [ctypes.c_char_p, ctypes.c_size_t, sz],
+        "tt_tune_import": [ctypes.c_char_p],
+        "tt_tune_clear": [],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -116,6 +125,8 @@ def load(path: str | None = None):
     lib.tt_trace.restype = ctypes.c_int
     lib.tt_trace_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
     lib.tt_trace_read.restype = ctypes.c_int
+    lib.tt_tune_generation.argtypes = []
+    lib.tt_tune_generation.restype = ctypes.c_uint64
     lib.tt_status_string.argtypes = [ctypes.c_int]
     lib.tt_status_string.restype = ctypes.c_char_p
     if path is None:

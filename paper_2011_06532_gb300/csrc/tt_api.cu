@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -194,7 +195,7 @@ int batch_layout(int32_t count, const tt_tensor *xs, int precision, BatchLayout 
     if (prec < 0) return TT_ERR_INVALID_ARG;
     size_t b = 0;
     if (xs[k].N > 1) {
-      const int st = ttgb::round_workspace(&xs[k], prec, &b);
+      const int st = ttgb::round_workspace(&xs[k], prec, &b, ttgb::kCtxBatch);
       if (st) return st;
     }
     mx = b > mx ? b : mx;
@@ -229,14 +230,32 @@ int batch_enqueue(int32_t count, const tt_tensor *xs, const double *eps, int pre
   if (cudaEventRecord(bs->fork, stream) != cudaSuccess) return TT_ERR_CUDA;
   for (int s = 0; s < lay.slots; ++s)
     if (cudaStreamWaitEvent(bs->s[s], bs->fork, 0) != cudaSuccess) return TT_ERR_CUDA;
-  size_t roff = 0;
+  // Members go to the internal streams largest first, each to the stream with the least
+  // work queued so far (longest-processing-time rule), so that one stream does not end
+  // up with several of the largest members.  Work ~ sum_n R_{n-1} I_n R_n max(R_{n-1}, R_n).
+  std::vector<size_t> roff(count);
+  std::vector<double> cost(count);
+  std::vector<int> order(count);
+  size_t acc = 0;
   for (int k = 0; k < count; ++k) {
-    const int slot = k % lay.slots;
+    roff[k] = acc;
+    acc += (size_t)xs[k].N + 1;
+    double c = 0.0;
+    for (int n = 0; n < xs[k].N; ++n)
+      c += (double)xs[k].R[n] * (double)xs[k].I[n] * (double)xs[k].R[n + 1] *
+           (double)std::max(xs[k].R[n], xs[k].R[n + 1]);
+    cost[k] = c;
+    order[k] = k;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<double> load(lay.slots, 0.0);
+  for (int k : order) {
+    const int slot = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[slot] += cost[k];
     st = ttgb::round_enqueue(&xs[k], eps[k], resolve_prec(&xs[k], precision), &outs[k],
-                             ws + (size_t)slot * lay.slot_bytes, lay.slot_bytes, bs->s[slot], ranks_dev + roff,
-                             status_dev + k);
+                             ws + (size_t)slot * lay.slot_bytes, lay.slot_bytes, bs->s[slot], ranks_dev + roff[k],
+                             status_dev + k, ttgb::kCtxBatch);
     if (st) return st;
-    roff += (size_t)xs[k].N + 1;
   }
   for (int s = 0; s < lay.slots; ++s) {
     if (cudaEventRecord(bs->join[s], bs->s[s]) != cudaSuccess) return TT_ERR_CUDA;

@@ -3,15 +3,44 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
 
 #include "tt.h"
 
 namespace ttgb {
 
-int round_workspace(const tt_tensor *x, int prec, size_t *bytes);
+// Plans are made for a context: a rounding on its own (kCtxSolo) or a member of a batch,
+// whose roundings share the GPU with the other members (kCtxBatch).
+constexpr int kCtxSolo = 0, kCtxBatch = 1;
+
+int round_workspace(const tt_tensor *x, int prec, size_t *bytes, int ctx = kCtxSolo);
 int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st);
 int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes,
-                  cudaStream_t st, int *ranks_dev, int *status_dev);
+                  cudaStream_t st, int *ranks_dev, int *status_dev, int ctx = kCtxSolo);
+
+// ---- tile choices --------------------------------------------------------------------
+// A core is planned from its shape class: precision, context, mode size and the ranks
+// around it before (R0, R1) and after (K0, K1) the orthogonalization sweep.
+struct TileKey {
+  int prec = 0, ctx = 0;
+  int64_t I = 0;
+  int R0 = 0, R1 = 0, K0 = 0, K1 = 0;
+  bool operator<(const TileKey &o) const;
+  bool operator==(const TileKey &o) const;
+};
+// P = leaves (CTAs) over the mode, Tt = slices per leaf tile; 0 = the built-in heuristic.
+struct TileChoice {
+  int P = 0, Tt = 0;
+};
+// The choice for a key: the calling thread's trial choices while it is tuning, else the
+// tuned table; false when neither has one.
+bool tile_choice(const TileKey &k, TileChoice *c);
+// Every core class of x under precision prec, with the heuristic's choice for each.
+int tile_classes(const tt_tensor *x, int prec, int ctx, std::vector<TileKey> *keys,
+                 std::vector<TileChoice> *heuristic, std::vector<int64_t> *elems);
+int device_sm_count();
 int norm_workspace(const tt_tensor *x, size_t *bytes);
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st);
 

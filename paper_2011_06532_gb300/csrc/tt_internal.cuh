@@ -201,6 +201,37 @@ __device__ __forceinline__ df32 warp_sum<df32>(df32 v) {
   return v;
 }
 
+// ------------------------------------------------------------------------------------
+// exponent range of carried factors
+// ------------------------------------------------------------------------------------
+// A TT's norm is a product of N per-core factors, so the small matrices carried from core
+// to core (the pushed R of the orthogonalization, the partial contraction W of the inner
+// product) can drift by a fixed factor per core: a Hadamard product of two unit-norm TTs
+// with 30 modes of size 1024 has norm near 2^-150, out of FP32 range.  Carried factors are
+// therefore kept in [2^-32, 2^32] by exact power-of-two rescaling, and the exponent is
+// accumulated separately.
+
+// Largest |v[i]| over the block (any block size that is a multiple of 32, up to 1024).
+__device__ __forceinline__ double block_absmax(const double *v, int n, double *red32) {
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(v[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red32[threadIdx.x >> 5] = m;
+  __syncthreads();
+  double r = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, red32[w]);
+  __syncthreads();
+  return r;
+}
+
+// Power-of-two exponent to divide out of a factor whose largest entry is m: zero while m
+// stays in [2^-32, 2^32] (and for a zero or non-finite factor), else the binary exponent of m.
+__device__ __forceinline__ int range_exp(double m) {
+  if (!(m > 0.0) || !isfinite(m) || (m >= 0x1p-32 && m <= 0x1p32)) return 0;
+  return ilogb(m);
+}
+
 // Scratch a block-level routine needs in shared memory.
 template <typename T>
 struct Scratch {

@@ -131,13 +131,18 @@ constexpr int kDotBlocks = 304;  // CTAs per core (2 per SM); partial sums are r
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot_core(const T *__restrict__ X, const T *__restrict__ Y, int64_t I, int rx0,
                                                   int rx1, int ry0, int ry1, const double *__restrict__ W,
-                                                  double *__restrict__ partial) {
+                                                  double *__restrict__ partial, int *E) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *Ws = reinterpret_cast<T *>(smem);
   T *Zs = Ws + ry0 * rx0;
   double *acc = reinterpret_cast<double *>(smem + ((sizeof(T) * (size_t)(ry0 * rx0 + ry0 * rx1) + 15) / 16) * 16);
+  __shared__ double red[8];
   const int t = threadIdx.x;
-  for (int idx = t; idx < ry0 * rx0; idx += blockDim.x) Ws[idx] = (T)W[idx];
+  // W_{n-1} enters in [2^-32, 2^32] up to an exact power of two, accumulated in E (every
+  // block finds the same exponent; block 0 records it)
+  const int e = range_exp(block_absmax(W, ry0 * rx0, red));
+  for (int idx = t; idx < ry0 * rx0; idx += blockDim.x) Ws[idx] = (T)ldexp(W[idx], -e);
+  if (blockIdx.x == 0 && t == 0 && e != 0) *E += e;
   for (int idx = t; idx < ry1 * rx1; idx += blockDim.x) acc[idx] = 0.0;
   __syncthreads();
   const int64_t s0 = (int64_t)blockIdx.x * I / gridDim.x, s1 = (int64_t)(blockIdx.x + 1) * I / gridDim.x;
@@ -173,8 +178,15 @@ __global__ void k_dot_reduce(const double *__restrict__ partial, int nblk, int n
   }
 }
 
-__global__ void k_dot_init(double *W) {
-  if (threadIdx.x == 0) W[0] = 1.0;
+__global__ void k_dot_init(double *W, int *E) {
+  if (threadIdx.x == 0) {
+    W[0] = 1.0;
+    *E = 0;
+  }
+}
+
+__global__ void k_dot_finish(double *W, const int *E) {
+  if (threadIdx.x == 0) W[0] = ldexp(W[0], *E);
 }
 
 static int dot_blocks(int64_t I) { return (int)std::min<int64_t>(I, kDotBlocks); }
@@ -191,14 +203,16 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
   size_t need = 0;
   dot_workspace(a, b, &need);
   if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
-  int64_t maxw = 1;
+  int64_t maxw = 1, maxp = 1;
   for (int n = 0; n <= a->N; ++n) maxw = std::max<int64_t>(maxw, a->R[n] * b->R[n]);
+  for (int n = 0; n < a->N; ++n) maxp = std::max<int64_t>(maxp, dot_blocks(a->I[n]) * a->R[n + 1] * b->R[n + 1]);
   double *W0 = reinterpret_cast<double *>(ws);
   double *W1 = W0 + maxw;
   double *part = W1 + maxw;
+  int *E = reinterpret_cast<int *>(part + maxp);  // exponent of the W rescaling
   {
     TraceScope ts_(TT_K_MISC, st);
-    k_dot_init<<<1, 32, 0, st>>>(W0);
+    k_dot_init<<<1, 32, 0, st>>>(W0, E);
   }
   TT_CUDA(cudaGetLastError());
   for (int n = 0; n < a->N; ++n) {
@@ -212,12 +226,12 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
       if (smem > 48 * 1024)
         TT_CUDA(cudaFuncSetAttribute(k_dot_core<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_dot_core<double><<<nb, 256, smem, st>>>((const double *)a->cores[n], (const double *)b->cores[n], a->I[n],
-                                                  rx0, rx1, ry0, ry1, W0, part);
+                                                  rx0, rx1, ry0, ry1, W0, part, E);
     } else {
       if (smem > 48 * 1024)
         TT_CUDA(cudaFuncSetAttribute(k_dot_core<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_dot_core<float><<<nb, 256, smem, st>>>((const float *)a->cores[n], (const float *)b->cores[n], a->I[n], rx0,
-                                                 rx1, ry0, ry1, W0, part);
+                                                 rx1, ry0, ry1, W0, part, E);
     }
     TT_CUDA(cudaGetLastError());
     {
@@ -227,6 +241,11 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
     TT_CUDA(cudaGetLastError());
     std::swap(W0, W1);
   }
+  {
+    TraceScope ts_(TT_K_MISC, st);
+    k_dot_finish<<<1, 32, 0, st>>>(W0, E);
+  }
+  TT_CUDA(cudaGetLastError());
   TT_CUDA(cudaMemcpyAsync(result, W0, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CUDA(cudaStreamSynchronize(st));
   return TT_OK;

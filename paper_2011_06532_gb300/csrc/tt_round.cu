@@ -98,6 +98,8 @@ struct S2Args {
   T *vtau;              // I x K1
   double *Rleaf;        // P x K1*K1
   S *out;               // last core output (L x I x 1)
+  const int *E;         // exponent gathered by the sweep-1 rescaling (see out_scale)
+  int n, N;             // index of the core written, number of cores
   int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv;
   int ldq, ldv;
   T *gscr;
@@ -115,6 +117,8 @@ struct OutArgs {
   const double *Uleaf;  // per leaf: U (k'_leaf x Lnext), leading dim ldc
   int ldc;
   S *out;               // output core n: L[n] x I x L[n+1]
+  const int *E;         // exponent gathered by the sweep-1 rescaling (see out_scale)
+  int n, N;
   int oV, oCT, oCR, oRed, oW, oSc, oTau;
   int ldv;
   T *gscr;
@@ -129,7 +133,8 @@ struct SvdArgs {
   int *Lnext;           // &L[n+1]
   int n, N;
   double eps;
-  double *scal;         // [0] = ||X||, [1] = delta
+  double *scal;         // [0] = ||X||, [1] = delta in the rescaled units of the sweep
+  const int *E;         // exponent gathered by the sweep-1 rescaling: ||X|| = 2^E ||X~_1||
   double *Uhat;         // k_root x K (ld ldu)
   double *Cnext;        // K x K (ld ldu)
   int ldu;
@@ -370,6 +375,22 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
 //               (last) apply Q_{N-1} and write the last output core
 // ------------------------------------------------------------------------------------
 
+// Factor 2^sh that output core n (of N) takes from the exponent E gathered by the sweep-1
+// rescaling.  The last core takes all of it when the storage type holds 2^E comfortably
+// (always in FP64); in FP32 storage a larger |E| is spread over the cores in near-equal
+// integer parts summing to E, so that no stored core leaves the FP32 range (the cores
+// before the last are then orthonormal up to their power-of-two factor).
+template <typename S>
+__device__ __forceinline__ S out_scale(const int *E, int n, int N) {
+  const int e = E ? *E : 0;
+  int sh;
+  if (sizeof(S) == 8 || (e >= -64 && e <= 64))
+    sh = n == N - 1 ? e : 0;
+  else
+    sh = (int)(((int64_t)e * (n + 1)) / N - ((int64_t)e * n) / N);
+  return (S)ldexp(1.0, sh);
+}
+
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -383,6 +404,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   const int K1 = a.K1;
   const int L = a.mode == 1 ? 1 : *a.Lcur;  // rows per slice of V(Y_n)
   const int b1 = a.b1;
+  const S osc = a.mode == 2 ? out_scale<S>(a.E, a.n, a.N) : S(1);
   // number of sweep-1 reflector rows owned by this leaf, and its C rows
   int kq = 0;
   if (a.mode != 1) {
@@ -426,7 +448,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
         // last core: Y[l, i, 0] = CT[(i - i0)][l]  (K1 == 1)
         for (int idx = t; idx < nt * L; idx += NT) {
           const int il = idx / L, l = idx - il * L;
-          a.out[(size_t)l + (size_t)L * (i0 + il)] = (S)CT[il * L + l];
+          a.out[(size_t)l + (size_t)L * (i0 + il)] = (S)CT[il * L + l] * osc;
         }
         __syncthreads();
         continue;
@@ -487,6 +509,7 @@ __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
   const int p = blockIdx.x, t = threadIdx.x;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
   const int K1 = a.K1, L = *a.Lcur, Ln = *a.Lnext;
+  const S osc = out_scale<S>(a.E, a.n, a.N);
   const int kleaf = (int)min64((s1 - s0) * (int64_t)L, K1);
   const double *Up = a.Uleaf + (size_t)p * K1 * a.ldc;
   for (int idx = t; idx < K1 * Ln; idx += NT) {
@@ -516,7 +539,7 @@ __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
     // rows (i - i0) * L + l, column l'  ->  out[l + L (i + I l')]
     for (int idx = t; idx < Mv * Ln; idx += NT) {
       const int c = idx / Mv, r = idx - c * Mv;
-      a.out[(size_t)L * i0 + r + (size_t)L * a.g.I * c] = (S)CT[r * Ln + c];
+      a.out[(size_t)L * i0 + r + (size_t)L * a.g.I * c] = (S)CT[r * Ln + c] * osc;
     }
     __syncthreads();
   }
@@ -794,7 +817,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
       double s2 = 0.0;
       for (int i = ns - 1; i >= 0; --i) s2 += sig[ord[i]] * sig[ord[i]];
       const double nrm = sqrt(s2);
-      a.scal[0] = nrm;
+      a.scal[0] = ldexp(nrm, *a.E);
       a.scal[1] = a.N > 1 ? a.eps * nrm / sqrt((double)(a.N - 1)) : 0.0;
     }
     const double d2 = a.scal[1] * a.scal[1];
@@ -867,12 +890,21 @@ __global__ void k_init_ctl(int *L, int N, int *status) {
   if (threadIdx.x < 4) status[threadIdx.x] = 0;
 }
 
-__global__ void k_sum_sqrt(const double *partial, int n, double *out) {
+__global__ void k_sum_sqrt(const double *partial, int n, const int *E, double *out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += partial[i];
-    out[0] = sqrt(s);
+    out[0] = ldexp(sqrt(s), *E);
   }
+}
+
+// Moves the root factor of sweep 1 (n entries) to the pushed-factor region, dividing it by
+// 2^e when its largest entry leaves [2^-32, 2^32] and adding e to E.
+__global__ void __launch_bounds__(256) k_take_root(const double *root, int n, double *keep, int *E) {
+  __shared__ double red[8];
+  const int e = range_exp(block_absmax(root, n, red));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keep[i] = ldexp(root[i], -e);
+  if (threadIdx.x == 0 && e != 0) *E += e;
 }
 
 // ------------------------------------------------------------------------------------
@@ -1081,10 +1113,23 @@ struct CorePlan {
   int R0 = 1, R1 = 1;  // input ranks
   int K0 = 1, K1 = 1;  // ranks after sweep 1
   int P = 1, Tt = 1;
+  int Tt_want = 0;     // tuned tile (0 = heuristic); clamped to what fits
   bool spill = false;  // running factor / carried block in global scratch
   Tree tree;
   size_t refl_off = 0, tau_off = 0, slot_off = 0;  // sweep-1 storage (n >= 1)
 };
+
+TileKey core_key(const CorePlan &c, int prec, int ctx) {
+  TileKey k;
+  k.prec = prec;
+  k.ctx = ctx;
+  k.I = c.I;
+  k.R0 = c.R0;
+  k.R1 = c.R1;
+  k.K0 = c.K0;
+  k.K1 = c.K1;
+  return k;
+}
 
 }  // namespace
 
@@ -1105,7 +1150,7 @@ struct RoundPlan {
   int tree_MT[TT_MAX_RANK + 1];
 };
 
-static int device_sm_count() {
+int device_sm_count() {
   int dev = 0, n = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 152;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
@@ -1169,10 +1214,15 @@ static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
     }
     if (best == 0) return false;
     c.Tt = best;
-    for (int Tt = best; Tt >= 1; --Tt) {
-      if (core_smem<T>(pl, n, Tt, c.spill, sweep1_only, nullptr) <= kSmemPair) {
-        c.Tt = Tt;
-        break;
+    if (c.Tt_want > 0) {
+      c.Tt = std::min(best, c.Tt_want);
+    } else {
+      // heuristic: the largest tile that lets two leaves share an SM
+      for (int Tt = best; Tt >= 1; --Tt) {
+        if (core_smem<T>(pl, n, Tt, c.spill, sweep1_only, nullptr) <= kSmemPair) {
+          c.Tt = Tt;
+          break;
+        }
       }
     }
     size_t g = 0;
@@ -1183,7 +1233,7 @@ static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
 }
 
 template <typename T>
-static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false) {
+static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int prec, int ctx) {
   const int N = x->N;
   pl.N = N;
   pl.keep_q = !sweep1_only;
@@ -1209,6 +1259,11 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
   for (int n = 0; n < N; ++n) {
     CorePlan &c = pl.core[n];
     c.P = leaves_for(c.I, pl.nsm);
+    TileChoice tc;
+    if (tile_choice(core_key(c, prec, ctx), &tc)) {
+      if (tc.P > 0) c.P = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)tc.P, c.I, (int64_t)1 << kMaxLev}));
+      c.Tt_want = tc.Tt;
+    }
     c.tree = make_tree(c.P);
   }
   if (N > 1 && !choose_tiles<T>(pl, sweep1_only)) return TT_ERR_UNSUPPORTED;
@@ -1257,18 +1312,42 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only = false
 }
 
 // compute type of each precision: FP64 -> double, FP32X2 -> df32 (pairs of floats), FP32 -> float
-static int plan_for(const tt_tensor *x, int prec, RoundPlan &pl, bool sweep1_only) {
+static int plan_for(const tt_tensor *x, int prec, RoundPlan &pl, bool sweep1_only, int ctx = kCtxSolo) {
   switch (prec) {
-    case TT_PREC_FP64: return make_plan<double>(x, pl, sweep1_only);
-    case TT_PREC_FP32X2: return make_plan<df32>(x, pl, sweep1_only);
-    case TT_PREC_FP32: return make_plan<float>(x, pl, sweep1_only);
+    case TT_PREC_FP64: return make_plan<double>(x, pl, sweep1_only, prec, ctx);
+    case TT_PREC_FP32X2: return make_plan<df32>(x, pl, sweep1_only, prec, ctx);
+    case TT_PREC_FP32: return make_plan<float>(x, pl, sweep1_only, prec, ctx);
     default: return TT_ERR_INVALID_ARG;
   }
 }
 
-int round_workspace(const tt_tensor *x, int prec, size_t *bytes) {
+int tile_classes(const tt_tensor *x, int prec, int ctx, std::vector<TileKey> *keys, std::vector<TileChoice> *heur,
+                 std::vector<int64_t> *elems) {
+  keys->clear();
+  heur->clear();
+  elems->clear();
+  if (x->N < 2) return TT_OK;
   RoundPlan pl;
-  int st = plan_for(x, prec, pl, false);
+  int st = plan_for(x, prec, pl, false, ctx);
+  if (st) return st;
+  for (const CorePlan &c : pl.core) {
+    const TileKey k = core_key(c, prec, ctx);
+    const int64_t e = (int64_t)c.R0 * c.I * c.R1;
+    size_t i = 0;
+    while (i < keys->size() && !((*keys)[i] == k)) ++i;
+    if (i == keys->size()) {
+      keys->push_back(k);
+      heur->push_back(TileChoice{leaves_for(c.I, pl.nsm), 0});
+      elems->push_back(0);
+    }
+    (*elems)[i] += e;
+  }
+  return TT_OK;
+}
+
+int round_workspace(const tt_tensor *x, int prec, size_t *bytes, int ctx) {
+  RoundPlan pl;
+  int st = plan_for(x, prec, pl, false, ctx);
   if (st) return st;
   *bytes = pl.total;
   return TT_OK;
@@ -1379,7 +1458,7 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
 }
 
 template <typename S, typename T>
-static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st) {
+static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st, int *E) {
   const int N = pl.N;
   const int B = pl.bmax;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
@@ -1424,7 +1503,11 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     double *root = Rbase + c.tree.node_off[c.tree.nlev] * B * B;
     double *keep = reinterpret_cast<double *>(ws + pl.off_P);
     // root is b x b row-major with K0 valid rows; the push needs K0 x R0 with ld R0 == b
-    TT_CUDA(cudaMemcpyAsync(keep, root, sizeof(double) * (size_t)c.R0 * c.R0, cudaMemcpyDeviceToDevice, st));
+    {
+      TraceScope ts_(TT_K_MISC, st);
+      k_take_root<<<1, 256, 0, st>>>(root, c.R0 * c.R0, keep, E);
+    }
+    TT_CUDA(cudaGetLastError());
     Pm = keep;
   }
   return TT_OK;
@@ -1447,7 +1530,8 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     k_init_ctl<<<1, 32, 0, st>>>(dL, N, dstatus);
   }
   TT_CUDA(cudaGetLastError());
-  int r = sweep1<S, T>(pl, x, ws, st);
+  int *dE = dstatus + 2;  // exponent of the sweep-1 rescaling (zeroed above)
+  int r = sweep1<S, T>(pl, x, ws, st, dE);
   if (r) return r;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
   double *C1 = reinterpret_cast<double *>(ws + pl.off_C1);
@@ -1530,6 +1614,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.N = N;
       a.eps = eps;
       a.scal = dscal;
+      a.E = dE;
       a.Uhat = C2 + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
       a.Cnext = C1 + cn.tree.node_off[cn.tree.nlev] * (size_t)B * B;
       a.ldu = B;
@@ -1561,6 +1646,9 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.Uleaf = C2 + c.tree.node_off[0] * (size_t)B * B;
       a.ldc = B;
       a.out = reinterpret_cast<S *>(out->cores[n]);
+      a.E = dE;
+      a.n = n;
+      a.N = N;
       a.oV = m.oV;
       a.oCT = m.oCT;
       a.oCR = m.oCR;
@@ -1598,6 +1686,9 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     a.ldc = B;
     a.Lcur = dL + N - 1;
     a.out = reinterpret_cast<S *>(out->cores[N - 1]);
+    a.E = dE;
+    a.n = N - 1;
+    a.N = N;
     a.oQ = m.oQ;
     a.oCT = m.oCT;
     a.oCR = m.oCR;
@@ -1641,7 +1732,7 @@ __global__ void k_ranks_one(int *ranks, int *status) {
 }
 
 int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes,
-                  cudaStream_t st, int *ranks_dev, int *status_dev) {
+                  cudaStream_t st, int *ranks_dev, int *status_dev, int ctx) {
   if (x->N == 1) {
     const size_t es = x->dtype == TT_F64 ? 8 : 4;
     TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDeviceToDevice, st));
@@ -1656,7 +1747,7 @@ int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void
     return TT_OK;
   }
   RoundPlan pl;
-  int r = plan_for(x, prec, pl, false);
+  int r = plan_for(x, prec, pl, false, ctx);
   if (r) return r;
   if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
   unsigned char *w = reinterpret_cast<unsigned char *>(ws);
@@ -1684,7 +1775,9 @@ int norm_workspace(const tt_tensor *x, size_t *bytes) {
 template <typename S, typename T>
 static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, unsigned char *ws, cudaStream_t st) {
   const int N = pl.N;
-  int r = N > 1 ? sweep1<S, T>(pl, x, ws, st) : TT_OK;
+  int *dE = reinterpret_cast<int *>(ws + pl.off_status) + 2;
+  TT_CUDA(cudaMemsetAsync(dE, 0, sizeof(int), st));
+  int r = N > 1 ? sweep1<S, T>(pl, x, ws, st, dE) : TT_OK;
   if (r) return r;
   const CorePlan &c0 = pl.core[0];
   double *part = reinterpret_cast<double *>(ws + pl.off_part);
@@ -1701,7 +1794,7 @@ static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, uns
   TT_CUDA(cudaGetLastError());
   {
     TraceScope ts_(TT_K_MISC, st);
-    k_sum_sqrt<<<1, 32, 0, st>>>(part, blocks, res);
+    k_sum_sqrt<<<1, 32, 0, st>>>(part, blocks, dE, res);
   }
   TT_CUDA(cudaGetLastError());
   TT_CUDA(cudaMemcpyAsync(result, res, sizeof(double), cudaMemcpyDeviceToHost, st));

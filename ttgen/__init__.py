@@ -285,3 +285,21 @@ def device_perturbed_pair(I: Sequence[int], r: int, seed: int, device="cuda"):
     _, _, Z = device_random_tt(I, R, seed + 1000, device)
     Yp = [(0.5 if n == 0 else 1.0) * Y[n] + 1e-9 * Z[n] for n in range(N)]
     return (list(I), R, Y), (list(I), R, Yp)
+
+
+def hadamard_pair_shapes(count: int = 64, seed: int = BASE_SEED + 5):
+    """(r_A, r_B) per pair of the Hadamard pipeline recipe: U{4..12} each, pair 0 fixed 8 x 8."""
+    out = [(8, 8)]
+    for p in range(1, count):
+        u = uniforms(2, seed, 1 << 22, p)
+        out.append((uniform_int(u[0], 4, 12), uniform_int(u[1], 4, 12)))
+    return out
+
+
+def hadamard_pair(p: int, N: int = 30, I: int = 1024, count: int = 64, seed: int = BASE_SEED + 5):
+    """Random TTs A_p, B_p (N modes of size I) with the ranks of hadamard_pair_shapes;
+    the pipeline forms Z = A o B, rounds it, then takes <Y, Z> and ||Y||."""
+    ra, rb = hadamard_pair_shapes(count, seed)[p]
+    A = random_tt([I] * N, uniform_ranks(N, ra), seed + 2 * p, stream=1)
+    B = random_tt([I] * N, uniform_ranks(N, rb), seed + 2 * p + 1, stream=2)
+    return A, B
