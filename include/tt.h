@@ -76,7 +76,8 @@ typedef struct {
   const int64_t *I;     /* host array [N], mode sizes, each >= 1 */
   int64_t *R;           /* host array [N+1], ranks, R[0] = R[N] = 1, each >= 1;
                            written by routines that produce this tensor */
-  void *const *cores;   /* host array [N] of device pointers, core n holds
+  void *const *cores;   /* host array [N] of device pointers (tt_round also takes
+                           mapped page-locked host memory), core n holds
                            R[n] * I[n] * R[n+1] elements of dtype */
 } tt_tensor;
 
@@ -106,6 +107,15 @@ int tt_round_workspace_size(const tt_tensor *x, int precision, size_t *bytes);
  *        tt_round_workspace_size(x) bytes (256-byte aligned).
  * N = 1 copies the single core.  A zero tensor returns ranks all 1 and zero
  * cores.  Synchronizes `stream` before returning.
+ *
+ * Host memory: the cores of x and of out may also be page-locked host memory
+ * mapped into the device's address space (cudaHostAlloc, or cudaHostRegister
+ * with unified addressing), as well as memory of the current device or managed
+ * memory.  The kernels then read each input core once and write each output core
+ * once over the host link, with no staging copy: the orthogonalization sweep
+ * reads every core exactly once and the arithmetic (not the link) bounds it.
+ * Any other pointer (unregistered host memory, another device's memory) returns
+ * TT_ERR_INVALID_ARG before anything is queued.
  */
 int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void *workspace, size_t workspace_bytes,
              void *stream);

@@ -85,9 +85,10 @@ def _stream(stream: Optional[torch.cuda.Stream]):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _validate(x: DeviceTT):
-    if not x.cores or any(not c.is_cuda for c in x.cores):
-        raise ValueError("cores must be CUDA tensors")
+def _validate(x: DeviceTT, host_ok: bool = False):
+    ok = (lambda c: c.is_cuda or (c.device.type == "cpu" and c.is_pinned())) if host_ok else (lambda c: c.is_cuda)
+    if not x.cores or any(not ok(c) for c in x.cores):
+        raise ValueError("cores must be CUDA tensors" + (" or pinned host tensors" if host_ok else ""))
     if any(c.dtype != x.cores[0].dtype for c in x.cores) or x.cores[0].dtype not in _DTYPES:
         raise ValueError("cores must all be float64 or all float32")
     for n, c in enumerate(x.cores):
@@ -119,17 +120,25 @@ def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tens
              workspace: Optional[torch.Tensor] = None, precision: str = "default") -> DeviceTT:
     """TT rounding (Alg. 2 / Alg. 6): returns Y with ||X - Y|| <= eps ||X||.
 
-    precision: "default", "fp64" (float64 cores), "fp32x2" or "fp32" (float32 cores)."""
-    _validate(x)
+    precision: "default", "fp64" (float64 cores), "fp32x2" or "fp32" (float32 cores).
+    Cores (of x and of out) may be CUDA tensors or pinned host tensors; the kernels read
+    and write pinned host cores directly over the host link.  Without `out`, the result
+    cores are allocated where x's are."""
+    _validate(x, host_ok=True)
+    if out is not None:
+        _validate(DeviceTT(list(x.I), list(x.R), list(out)), host_ok=True)
     lib = _native.load()
-    dev = x.cores[0].device
+    dev = x.cores[0].device if x.cores[0].is_cuda else torch.device("cuda", torch.cuda.current_device())
     prec = PRECISIONS[precision]
     d = _Desc(x.I, x.R, x.cores, x.dtype)
     n = ctypes.c_size_t(0)
     _check(lib.tt_round_workspace_size(d.ref, prec, ctypes.byref(n)), "tt_round_workspace_size")
     ws = workspace if workspace is not None else _workspace(int(n.value), dev)
     if out is None:
-        out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
+        if x.cores[0].is_cuda:
+            out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
+        else:
+            out = [torch.empty(s, dtype=x.dtype, pin_memory=True) for s in x.core_sizes()]
     o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
     _check(lib.tt_round(d.ref, float(eps), prec, o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
                         _stream(stream)), "tt_round")

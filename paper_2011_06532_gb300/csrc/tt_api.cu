@@ -46,6 +46,32 @@ bool same_modes(const tt_tensor *a, const tt_tensor *b) {
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Whether the current device can dereference p at that same address: memory of this
+// device, managed memory, or page-locked host memory mapped into the device's address
+// space (cudaHostAlloc / cudaHostRegister under unified addressing), which kernels read
+// and write over the host link.  Unregistered host memory is refused.
+bool device_accessible(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  switch (at.type) {
+    case cudaMemoryTypeDevice: return at.device == dev;
+    case cudaMemoryTypeManaged: return true;
+    case cudaMemoryTypeHost: return at.devicePointer == p;
+    default: return false;
+  }
+}
+
+bool cores_accessible(const tt_tensor *x) {
+  for (int n = 0; n < x->N; ++n)
+    if (!device_accessible(x->cores[n])) return false;
+  return true;
+}
+
 // resolves TT_PREC_DEFAULT and checks that the precision fits the element type; -1 if not
 int resolve_prec(const tt_tensor *x, int prec) {
   if (prec == TT_PREC_DEFAULT) return x->dtype == TT_F64 ? TT_PREC_FP64 : TT_PREC_FP32X2;
@@ -148,6 +174,7 @@ int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void
   const int prec = resolve_prec(x, precision);
   if (prec < 0) return TT_ERR_INVALID_ARG;
   if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (!cores_accessible(x) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
   return ttgb::round_run(x, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
 }
 

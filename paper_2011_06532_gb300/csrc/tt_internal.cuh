@@ -308,20 +308,21 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
 // 0..k-1 hold updated R rows; tile entries (r, c) with c < k + r hold reflector entries
 // and, for r < kk - k, entries c >= k + r hold R row k + r.  tau[0..kk-1] is written.
 // Rr and tile are row-major with leading dimensions ldr, ldt.  Returns kk.
-// tri_off >= 0 declares the tile upper trapezoidal with row r starting at column
-// r + tri_off (a triangular factor stacked under Rr): reflector j then only touches tile
-// rows r <= j - tri_off, the others being zero in column j.  tri_off < 0: dense tile.
-__device__ __forceinline__ int tile_rows_for(int j, int M, int tri_off) {
-  return tri_off < 0 ? M : min(M, max(0, j - tri_off + 1));
+// tri_off >= 0 declares the tile as q upper-triangular factors interleaved row by row
+// (tile row r q + i is row r of factor i, starting at column r + tri_off): reflector j then
+// only touches tile rows < (j - tri_off + 1) q, the others being zero in column j.  q = 1
+// is a single triangle stacked under Rr.  tri_off < 0: dense tile.
+__device__ __forceinline__ int tile_rows_for(int j, int M, int tri_off, int q = 1) {
+  return tri_off < 0 ? M : min(M, max(0, (j - tri_off + 1) * q));
 }
 
 template <typename T>
 __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
-                         int tri_off = -1) {
+                         int tri_off = -1, int q = 1) {
   const int kk = min(k + M, b);
   for (int j = 0; j < kk; ++j) {
     const int r0 = j < k ? 0 : j - k + 1;
-    const int Mj = tile_rows_for(j, M, tri_off);
+    const int Mj = tile_rows_for(j, M, tri_off, q);
     T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
     if (threadIdx.x < 32) {
       T ss = T(0);
@@ -390,14 +391,14 @@ __device__ void hh_take_rows(T *Rr, int ldr, int k, int kk, const T *tile, int l
 // tau of that step (V row-major, ld ldv); tri_off as in hh_factor.
 template <typename T>
 __device__ void hh_apply(const T *V, int ldv, const T *tau, int k, int M, int b, T *CR, int ldcr, T *CT, int ldct,
-                         int nc, Scratch<T> s, int tri_off = -1) {
+                         int nc, Scratch<T> s, int tri_off = -1, int q = 1) {
   const int kk = min(k + M, b);
   for (int j = kk - 1; j >= 0; --j) {
     const T tj = tau[j];
     if (tj == T(0)) continue;
     const int r0 = j < k ? 0 : j - k + 1;
     T *piv = j < k ? CR + (size_t)j * ldcr : CT + (size_t)(j - k) * ldct;
-    reflect(tj, V + j, ldv, r0, tile_rows_for(j, M, tri_off), piv, CT, ldct, nc, s);
+    reflect(tj, V + j, ldv, r0, tile_rows_for(j, M, tri_off, q), piv, CT, ldct, nc, s);
   }
 }
 

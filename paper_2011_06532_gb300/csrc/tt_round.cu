@@ -264,6 +264,17 @@ __device__ __forceinline__ int child_rows_k(const TreeArgs &a, int c, int rho) {
   return (int)min64(rows, a.b);
 }
 
+// A node whose children all carry full b x b triangles, with more than one triangle to
+// stack under the first and room for all of them in one tile, is factored (and applied)
+// in one pass over the interleaved triangles; any other node takes its children one by
+// one.  Factor and apply decide alike from the same arguments.
+__device__ __forceinline__ bool interleaved_node(const TreeArgs &a, int c0, int c1, int rho) {
+  if (c1 - c0 < 3 || (c1 - c0 - 1) * a.b > a.MT) return false;
+  for (int c = c0; c < c1; ++c)
+    if (child_rows_k(a, c, rho) != a.b) return false;
+  return true;
+}
+
 __global__ void __launch_bounds__(NT) k_tree_factor(TreeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   double *Rr = sm<double>(smem, a.oA), *tile = sm<double>(smem, a.oB);
@@ -275,6 +286,30 @@ __global__ void __launch_bounds__(NT) k_tree_factor(TreeArgs a) {
   int k = child_rows_k(a, c0, rho);
   const double *R0 = a.Rin + (size_t)c0 * b * b;
   for (int idx = t; idx < b * b; idx += NT) Rr[idx] = (idx / b) < k ? R0[idx] : 0.0;
+  if (interleaved_node(a, c0, c1, rho)) {
+    // all children full: the other q = c1 - c0 - 1 triangles, interleaved row by row, form
+    // one tile factored in a single pass of b reflectors
+    const int qq = c1 - c0 - 1, M = qq * b;
+    for (int idx = t; idx < M * b; idx += NT) {
+      const int row = idx / b, col = idx - row * b;
+      const int r = row / qq, i = row - r * qq;
+      tile[row * a.lda + col] = a.Rin[(size_t)(c0 + 1 + i) * b * b + (size_t)r * b + col];
+    }
+    __syncthreads();
+    hh_factor(Rr, b, b, tile, a.lda, M, b, taus, s, 0, qq);
+    if (a.slots) {
+      for (int idx = t; idx < M * b; idx += NT) {
+        const int row = idx / b, col = idx - row * b;
+        const int r = row / qq, i = row - r * qq;
+        a.slots[(size_t)(c0 + 1 + i) * (b * b + a.nchunk * b) + (size_t)r * b + col] = tile[row * a.lda + col];
+      }
+      for (int j = t; j < b; j += NT) a.slots[(size_t)(c0 + 1) * (b * b + a.nchunk * b) + (size_t)b * b + j] = taus[j];
+    }
+    __syncthreads();
+    double *Ro = a.Rout + (size_t)q * b * b;
+    for (int idx = t; idx < b * b; idx += NT) Ro[idx] = Rr[idx];
+    return;
+  }
   __syncthreads();
   for (int c = c0 + 1; c < c1; ++c) {
     const int kc = child_rows_k(a, c, rho);
@@ -330,6 +365,32 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
   for (int idx = t; idx < b * nc; idx += NT) {
     const int r = idx / nc, col = idx - r * nc;
     C[r * nc + col] = r < k ? Cn[(size_t)r * a.ldc + col] : 0.0;
+  }
+  if (interleaved_node(a, c0, c1, rho)) {
+    // Q [C; 0] with the interleaved tile of the factorization; child c0 + 1 + i receives
+    // rows r q + i of the lower block, child c0 the upper block
+    const int qq = c1 - c0 - 1, M = qq * b;
+    for (int idx = t; idx < M * b; idx += NT) {
+      const int row = idx / b, col = idx - row * b;
+      const int r = row / qq, i = row - r * qq;
+      V[row * a.lda + col] = a.slots[(size_t)(c0 + 1 + i) * (b * b + a.nchunk * b) + (size_t)r * b + col];
+    }
+    for (int j = t; j < b; j += NT) taus[j] = a.slots[(size_t)(c0 + 1) * (b * b + a.nchunk * b) + (size_t)b * b + j];
+    for (int idx = t; idx < M * nc; idx += NT) CT[idx] = 0.0;
+    __syncthreads();
+    hh_apply(V, a.lda, taus, b, M, b, C, nc, CT, nc, nc, s, 0, qq);
+    __syncthreads();
+    for (int idx = t; idx < M * nc; idx += NT) {
+      const int row = idx / nc, col = idx - row * nc;
+      const int r = row / qq, i = row - r * qq;
+      a.Cout[(size_t)(c0 + 1 + i) * b * a.ldc + (size_t)r * a.ldc + col] = CT[idx];
+    }
+    double *Cc0 = a.Cout + (size_t)c0 * b * a.ldc;
+    for (int idx = t; idx < b * nc; idx += NT) {
+      const int r = idx / nc, col = idx - r * nc;
+      Cc0[(size_t)r * a.ldc + col] = C[r * nc + col];
+    }
+    return;
   }
   __syncthreads();
   int step = nsteps;
@@ -596,13 +657,26 @@ __device__ __forceinline__ void jrot(float al, float be, float ga, float &c, flo
   sn = (h > 0.0f ? g : -g) * w;
 }
 
+// sum over the LP consecutive lanes of a segment (LP a power of two <= 32)
+template <int LP, typename T>
+__device__ __forceinline__ T seg_sum(T v) {
+#pragma unroll
+  for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Round-robin one-sided Jacobi on A (ms x ns, column-major), accumulating the rotations
 // into V (ns x ns, column-major).  pos holds 2 * (ns + 2) ints, flag 1 int.  Returns
 // whether a sweep completed without rotating.  Pairs whose two columns both have squared
 // norms <= neg2 are left alone (deflation of negligible columns).
+// Each pair is handled by a segment of LP = 8 lanes (4 pairs per warp): on GB300 an FP64
+// warp instruction costs the FP64 unit the same time whatever its active lanes, so the
+// per-pair dot products, reductions and rotation angle are packed four to an instruction.
 template <typename T>
 __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2) {
+  constexpr int LP = 8, PW = 32 / LP;  // lanes per pair, pairs per warp
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
+  const int seg = lane / LP, sl = lane - seg * LP;
   if (ns <= 1) return true;
   const int n2 = (ns + 1) & ~1;
   const int stride = ns + 2;
@@ -615,40 +689,45 @@ __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, i
     __syncthreads();
     for (int round = 0; round < n2 - 1; ++round) {
       const int *P = pos + cur * stride;
-      for (int pr = warp; pr < n2 / 2; pr += nwarp) {
-        int pp = P[pr], qq = P[n2 - 1 - pr];
-        if (pp >= ns || qq >= ns) continue;
+      // every lane of a warp runs the same number of iterations (the shuffles need the
+      // whole warp); segments without a pair in an iteration compute on dummy values
+      for (int base = warp * PW; base < n2 / 2; base += nwarp * PW) {
+        const int pr = base + seg;
+        int pp = pr < n2 / 2 ? P[pr] : ns, qq = pr < n2 / 2 ? P[n2 - 1 - pr] : ns;
+        const bool live = pp < ns && qq < ns;
         if (pp > qq) {
           const int tmp = pp;
           pp = qq;
           qq = tmp;
         }
-        T *bp = A + (size_t)pp * ms, *bq = A + (size_t)qq * ms;
+        T *bp = A + (size_t)(live ? pp : 0) * ms, *bq = A + (size_t)(live ? qq : 0) * ms;
         T al = 0, be = 0, ga = 0;
-        for (int r = lane; r < ms; r += 32) {
-          const T x = bp[r], y = bq[r];
-          al += x * x;
-          be += y * y;
-          ga += x * y;
+        if (live) {
+          for (int r = sl; r < ms; r += LP) {
+            const T x = bp[r], y = bq[r];
+            al += x * x;
+            be += y * y;
+            ga += x * y;
+          }
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga == T(0) || ga * ga <= tol2 * al * be || (al <= neg2 && be <= neg2)) continue;
+        al = seg_sum<LP>(al);
+        be = seg_sum<LP>(be);
+        ga = seg_sum<LP>(ga);
+        if (!live || ga == T(0) || ga * ga <= tol2 * al * be || (al <= neg2 && be <= neg2)) continue;
         T cs, sn;
         jrot(al, be, ga, cs, sn);
-        for (int r = lane; r < ms; r += 32) {
+        for (int r = sl; r < ms; r += LP) {
           const T x = bp[r], y = bq[r];
           bp[r] = cs * x - sn * y;
           bq[r] = sn * x + cs * y;
         }
         T *vp = V + (size_t)pp * ns, *vq = V + (size_t)qq * ns;
-        for (int r = lane; r < ns; r += 32) {
+        for (int r = sl; r < ns; r += LP) {
           const T x = vp[r], y = vq[r];
           vp[r] = cs * x - sn * y;
           vq[r] = sn * x + cs * y;
         }
-        if (lane == 0) flag[0] = 1;
+        if (sl == 0) flag[0] = 1;
       }
       __syncthreads();
       int *Pn = pos + (cur ^ 1) * stride;
@@ -913,7 +992,6 @@ __global__ void __launch_bounds__(256) k_take_root(const double *root, int n, do
 
 namespace {
 
-constexpr int kG = 2;          // tree fan-in (binary: fewest serial reflectors per root)
 constexpr int kMaxLev = 10;
 constexpr size_t kSmemBudget = 220 * 1024;
 constexpr size_t kSmemPair = 110 * 1024;  // two co-resident leaf CTAs per SM
@@ -931,6 +1009,7 @@ struct Carve {
 };
 
 struct Tree {
+  int G = 2;                  // fan-in (children per node)
   int nlev = 0;               // number of factor levels (0 if a single leaf)
   int count[kMaxLev + 1];     // count[0] = leaves, count[nlev] = 1
   int lpc[kMaxLev + 1];       // leaves per node at each level
@@ -940,14 +1019,15 @@ struct Tree {
   size_t nnodes = 0;
 };
 
-Tree make_tree(int P) {
+Tree make_tree(int P, int G) {
   Tree tr;
+  tr.G = G;
   tr.count[0] = P;
   tr.lpc[0] = 1;
   int l = 0;
   while (tr.count[l] > 1 && l < kMaxLev) {
-    tr.count[l + 1] = (tr.count[l] + kG - 1) / kG;
-    tr.lpc[l + 1] = tr.lpc[l] * kG;
+    tr.count[l + 1] = (tr.count[l] + G - 1) / G;
+    tr.lpc[l + 1] = tr.lpc[l] * G;
     ++l;
   }
   tr.nlev = l;
@@ -965,8 +1045,14 @@ Tree make_tree(int P) {
   return tr;
 }
 
-int leaves_for(int64_t I, int nsm) {
-  const int64_t target = std::min<int64_t>(2 * (int64_t)nsm, (int64_t)1 << kMaxLev);  // the tree holds 2^kMaxLev
+// Leaves of a core whose sweep-1 matrix has `rows` rows and b columns: two per SM, but no
+// fewer than 8 b rows per leaf while that still leaves one leaf per SM (below that the
+// tree's serial reflector chain costs more than the leaf work it spreads); at most I.
+int leaves_for(int64_t I, int64_t rows, int b, int nsm) {
+  int64_t target = 2 * (int64_t)nsm;
+  const int64_t by_rows = rows / (8 * (int64_t)std::max(b, 1));
+  if (by_rows < target) target = std::max<int64_t>(nsm, by_rows);
+  target = std::min<int64_t>(target, (int64_t)1 << kMaxLev);  // a binary tree holds 2^kMaxLev
   return (int)std::max<int64_t>(1, std::min<int64_t>(I, target));
 }
 
@@ -1074,11 +1160,13 @@ struct SmemTree {
   size_t bytes;
 };
 
-// factor: A = Rr (b x b), B = tile (MT x lda); apply: A = C (b x cmax), B = V (MT x lda) + CT (MT x cmax)
-SmemTree smem_tree(int b, int cmax) {
+// factor: A = Rr (b x b), B = tile (MT x lda); apply: A = C (b x cmax), B = V (MT x lda) + CT (MT x cmax).
+// The tile takes (G - 1) b rows (a node's other triangles at once) when that fits, else
+// b rows, else the largest halving of b that fits (a child in chunks).
+SmemTree smem_tree(int b, int cmax, int G) {
   SmemTree m;
   m.lda = b + 1;
-  for (m.MT = b; m.MT > 1; m.MT = (m.MT + 1) / 2) {
+  for (m.MT = std::max(1, G - 1) * b; m.MT > 1; m.MT = m.MT > b ? b : (m.MT + 1) / 2) {
     Carve c;
     size_t A = std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double);
     size_t B = ((size_t)m.MT * m.lda + (size_t)m.MT * cmax) * sizeof(double);
@@ -1100,6 +1188,17 @@ SmemTree smem_tree(int b, int cmax) {
   m.bytes = c.off;
   m.nchunk = (b + m.MT - 1) / m.MT;
   return m;
+}
+
+// Tree fan-in for factors of b columns: 4 children per node (one pass of b reflectors
+// over three interleaved triangles: half the serial reflectors of a binary tree from leaves
+// to root) when such a tile fits in shared memory, else 3, else 2.
+int tree_fanin(int b) {
+  for (int G : {4, 3}) {
+    const SmemTree m = smem_tree(b, b, G);
+    if (m.bytes <= kSmemBudget && m.MT >= (G - 1) * b) return G;
+  }
+  return 2;
 }
 
 // shared bytes of k_svd for K columns (ms = ns = K is the largest case)
@@ -1258,20 +1357,21 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
   pl.core[0].K0 = 1;
   for (int n = 0; n < N; ++n) {
     CorePlan &c = pl.core[n];
-    c.P = leaves_for(c.I, pl.nsm);
+    // the core's tall-skinny matrix: H(X_n)^T ((I K_{n+1}) x R_n) in sweep 1, V(X_1) (I x K_2) for core 1
+    c.P = n == 0 ? leaves_for(c.I, c.I, c.K1, pl.nsm) : leaves_for(c.I, c.I * c.K1, c.R0, pl.nsm);
     TileChoice tc;
     if (tile_choice(core_key(c, prec, ctx), &tc)) {
       if (tc.P > 0) c.P = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)tc.P, c.I, (int64_t)1 << kMaxLev}));
       c.Tt_want = tc.Tt;
     }
-    c.tree = make_tree(c.P);
+    c.tree = make_tree(c.P, std::min(tree_fanin(c.R0), tree_fanin(c.K1)));
   }
   if (N > 1 && !choose_tiles<T>(pl, sweep1_only)) return TT_ERR_UNSUPPORTED;
   // svd and tree shared-memory limits
   for (int n = 0; n + 1 < N && !sweep1_only; ++n)
     if (smem_svd(pl.core[n].K1, false) > kSmemBudget) return TT_ERR_UNSUPPORTED;
   for (int n = 1; n < N; ++n)
-    if (smem_tree(pl.core[n].R0, pl.core[n].R0).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
+    if (smem_tree(pl.core[n].R0, pl.core[n].R0, pl.core[n].tree.G).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
   // workspace layout
   Carve w;
   pl.off_L = w.take(sizeof(int) * (N + 1), 256);
@@ -1287,7 +1387,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
     if (n >= 1 && pl.keep_q) {
       c.refl_off = w.take(sizeof(T) * (size_t)c.I * c.K1 * c.R0, 256);
       c.tau_off = w.take(sizeof(T) * (size_t)c.I * c.R0, 256);
-      const SmemTree st = smem_tree(c.R0, c.R0);
+      const SmemTree st = smem_tree(c.R0, c.R0, c.tree.G);
       c.slot_off = w.take(sizeof(double) * c.tree.nslots * ((size_t)c.R0 * c.R0 + (size_t)st.nchunk * c.R0), 256);
     }
     if (n < N - 1) {
@@ -1337,7 +1437,7 @@ int tile_classes(const tt_tensor *x, int prec, int ctx, std::vector<TileKey> *ke
     while (i < keys->size() && !((*keys)[i] == k)) ++i;
     if (i == keys->size()) {
       keys->push_back(k);
-      heur->push_back(TileChoice{leaves_for(c.I, pl.nsm), 0});
+      heur->push_back(TileChoice{c.P, c.Tt});
       elems->push_back(0);
     }
     (*elems)[i] += e;
@@ -1368,7 +1468,7 @@ static int set_smem(K kernel, size_t bytes) {
 // level-by-level tree factorization of the leaf R's in Rbuf level 0; root ends at level nlev
 static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, double *Rbase, double *slots,
                        int B, cudaStream_t st) {
-  const SmemTree sm = smem_tree(b, b);  // same chunking as the apply (at most b columns)
+  const SmemTree sm = smem_tree(b, b, tr.G);  // same chunking as the apply (at most b columns)
   int r = set_smem(k_tree_factor, sm.bytes);
   if (r) return r;
   for (int l = 0; l < tr.nlev; ++l) {
@@ -1377,7 +1477,7 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
     a.Rout = Rbase + tr.node_off[l + 1] * B * B;
     a.slots = slots ? slots + tr.slot_off[l] * ((size_t)b * b + (size_t)sm.nchunk * b) : nullptr;
     a.nchild = tr.count[l];
-    a.G = kG;
+    a.G = tr.G;
     a.b = b;
     a.MT = sm.MT;
     a.nchunk = sm.nchunk;
@@ -1405,8 +1505,8 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
 // root-to-leaves application; the root C sits at Cbase level nlev; leaf C's end at level 0
 static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, int ncol, const int *ncol_dyn,
                       int cmax, double *Cbase, const double *slots, int B, cudaStream_t st) {
-  const SmemTree sm = smem_tree(b, cmax);
-  const SmemTree smf = smem_tree(b, b);  // the slots hold the factorization's chunking
+  const SmemTree sm = smem_tree(b, cmax, tr.G);
+  const SmemTree smf = smem_tree(b, b, tr.G);  // the slots hold the factorization's chunking
   SmemTree use = sm;
   use.MT = smf.MT;
   use.nchunk = smf.nchunk;
@@ -1420,7 +1520,7 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
     use.oTau = (int)c.take(sizeof(double) * b);
     use.bytes = c.off;
   }
-  if (use.bytes > kSmemBudget || kG * use.nchunk > 64) return TT_ERR_UNSUPPORTED;
+  if (use.bytes > kSmemBudget || tr.G * use.nchunk > 64) return TT_ERR_UNSUPPORTED;
   int r = set_smem(k_tree_apply, use.bytes);
   if (r) return r;
   for (int l = tr.nlev - 1; l >= 0; --l) {
@@ -1429,7 +1529,7 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
     a.Cout = Cbase + tr.node_off[l] * B * B;
     a.slots = const_cast<double *>(slots) + tr.slot_off[l] * ((size_t)b * b + (size_t)use.nchunk * b);
     a.nchild = tr.count[l];
-    a.G = kG;
+    a.G = tr.G;
     a.b = b;
     a.MT = use.MT;
     a.nchunk = use.nchunk;
@@ -1735,7 +1835,7 @@ int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void
                   cudaStream_t st, int *ranks_dev, int *status_dev, int ctx) {
   if (x->N == 1) {
     const size_t es = x->dtype == TT_F64 ? 8 : 4;
-    TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDeviceToDevice, st));
+    TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDefault, st));
     if (ranks_dev) {
       TraceScope ts_(TT_K_MISC, st);
       k_ranks_one<<<1, 32, 0, st>>>(ranks_dev, status_dev);
