@@ -246,8 +246,11 @@ struct Scratch {
 // trailing blocks still spread over the whole CTA); the partial dot products are summed by
 // a tree in shared memory, then w_c = tau (p_c + v^T X(:, c)) and X -= v w^T over the dense
 // block.  All threads of the CTA must call it with identical arguments; nc <= NT.
+// vscale: v = vscale * V (a reflector whose scaling is still pending); w and the update
+// are formed from the unscaled V.
 template <typename T>
-__device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, int ldx, int nc, Scratch<T> s) {
+__device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, int ldx, int nc, Scratch<T> s,
+                        T vscale = T(1)) {
   if (nc <= 0) return;
   const int t = threadIdx.x;
   const int nrow = M - r0;
@@ -273,8 +276,8 @@ __device__ void reflect(T tau, const T *V, int ldv, int r0, int M, T *p, T *X, i
     __syncthreads();
   }
   if (t < nc) {
-    const T w = tau * (p[t] + s.red[t]);
-    s.wbuf[t] = w;
+    const T w = tau * (p[t] + vscale * s.red[t]);
+    s.wbuf[t] = vscale * w;
     p[t] -= w;
   }
   __syncthreads();
@@ -320,10 +323,17 @@ template <typename T>
 __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
                          int tri_off = -1, int q = 1) {
   const int kk = min(k + M, b);
+  // the stored reflector of column pj still owes its scaling by pend (rows pr0..pM-1):
+  // the warps other than warp 0 apply it while warp 0 forms the next reflector
+  int pj = -1, pr0 = 0, pM = 0;
+  T pend = T(1);
   for (int j = 0; j < kk; ++j) {
     const int r0 = j < k ? 0 : j - k + 1;
     const int Mj = tile_rows_for(j, M, tri_off, q);
     T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
+    if (threadIdx.x >= 32 && pj >= 0) {
+      for (int r = pr0 + (int)threadIdx.x - 32; r < pM; r += NT - 32) tile[(size_t)r * ldt + pj] *= pend;
+    }
     if (threadIdx.x < 32) {
       T ss = T(0);
       for (int r = r0 + threadIdx.x; r < Mj; r += 32) {
@@ -361,15 +371,22 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
     }
     __syncthreads();
     const T tj = s.sc[1];
+    pj = -1;
     if (tj != T(0)) {
       const T scale = s.sc[0];
-      for (int r = r0 + threadIdx.x; r < Mj; r += NT) tile[(size_t)r * ldt + j] *= scale;
-      __syncthreads();
-      reflect(tj, tile + j, ldt, r0, Mj, piv + j + 1, tile + j + 1, ldt, b - j - 1, s);
+      reflect(tj, tile + j, ldt, r0, Mj, piv + j + 1, tile + j + 1, ldt, b - j - 1, s, scale);
+      pj = j;
+      pend = scale;
+      pr0 = r0;
+      pM = Mj;
     } else {
       __syncthreads();
     }
   }
+  if (pj >= 0) {
+    for (int r = pr0 + (int)threadIdx.x; r < pM; r += NT) tile[(size_t)r * ldt + pj] *= pend;
+  }
+  __syncthreads();
   return kk;
 }
 

@@ -1359,6 +1359,9 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
     CorePlan &c = pl.core[n];
     // the core's tall-skinny matrix: H(X_n)^T ((I K_{n+1}) x R_n) in sweep 1, V(X_1) (I x K_2) for core 1
     c.P = n == 0 ? leaves_for(c.I, c.I, c.K1, pl.nsm) : leaves_for(c.I, c.I * c.K1, c.R0, pl.nsm);
+    // a batch member shares the GPU with the members on the other streams: at most one
+    // leaf per two SMs by default (the batch tuner's usual pick)
+    if (ctx == kCtxBatch) c.P = std::min(c.P, std::max(1, pl.nsm / 2));
     TileChoice tc;
     if (tile_choice(core_key(c, prec, ctx), &tc)) {
       if (tc.P > 0) c.P = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)tc.P, c.I, (int64_t)1 << kMaxLev}));
