@@ -310,7 +310,43 @@ def run_variants(args):
     del X64, X32, ref
     torch.cuda.empty_cache()
     out["hadamard_pipeline"] = run_pipeline(args)
+    out["paper_model1"] = run_model1(args)
     return out
+
+
+def run_model1(args):
+    """The paper's TT Model 1 (Sec. 4, synthetic models: N=50 modes of size 2000, ranks 50
+    halved by the rounding), built the paper's way, Y = 2X - X with X a random rank-25 TT
+    (here via tt_add of two scaled copies), rounded at eps = 1e-8 (the paper states no
+    tolerance; any value between rounding error and the 25th singular value halves the
+    ranks).  Its single-node timing (Table 3: 9.2 s on one Skylake core, 0.27 s on 40) is
+    context for this row, not a ratio of the headline."""
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+    import ttgen
+
+    N, I, r = 50, 2000, 25
+    _, R, X = ttgen.device_random_tt([I] * N, ttgen.uniform_ranks(N, r), ttgen.BASE_SEED + 6)
+    two = ttgb.DeviceTT([I] * N, R, [2.0 * X[0]] + X[1:])
+    neg = ttgb.DeviceTT([I] * N, R, [-X[0]] + X[1:])
+    Y = ttgb.tt_add(two, neg)
+    del two, neg, X
+    res = {"N": N, "I": I, "formal_rank": 2 * r, "eps": 1e-8, "input_gb_fp64": Y.nbytes() / 1e9,
+           "paper_seconds": {"1 Skylake core": 9.2, "40 Skylake cores": 0.27}}
+    y = ttgb.tt_round(Y, 1e-8)
+    t = _time(lambda: ttgb.tt_round(Y, 1e-8), reps=3)
+    res["fp64"] = {"ms": t * 1e3, "ranks_max": max(y.R), "ranks_halved": max(y.R) == r}
+    Y32 = ttgb.DeviceTT(list(Y.I), list(Y.R), [c.float() for c in Y.cores])
+    ttgb._ws_cache.clear()
+    torch.cuda.empty_cache()
+    y32 = ttgb.tt_round(Y32, 1e-6, precision="fp32x2")
+    t32 = _time(lambda: ttgb.tt_round(Y32, 1e-6, precision="fp32x2"), reps=3)
+    res["fp32x2_eps1e-6"] = {"ms": t32 * 1e3, "ranks_max": max(y32.R)}
+    del Y, Y32, y, y32
+    ttgb._ws_cache.clear()
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_pipeline(args):

@@ -320,11 +320,12 @@ __device__ __forceinline__ int tile_rows_for(int j, int M, int tri_off, int q = 
 }
 
 template <typename T>
-__device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+__device__ int hh_factor_seq(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
                          int tri_off = -1, int q = 1) {
   const int kk = min(k + M, b);
-  // the stored reflector of column pj still owes its scaling by pend (rows pr0..pM-1):
-  // the warps other than warp 0 apply it while warp 0 forms the next reflector
+  // Narrow factors: warp 0 forms reflector j (column norm, square root, reciprocal) while
+  // the other warps apply the scaling still owed by the stored column of reflector pj
+  // (rows pr0..pM-1); then the whole CTA applies reflector j.
   int pj = -1, pr0 = 0, pM = 0;
   T pend = T(1);
   for (int j = 0; j < kk; ++j) {
@@ -388,6 +389,147 @@ __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, 
   }
   __syncthreads();
   return kk;
+}
+
+template <typename T>
+__device__ int hh_factor_ahead(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+                         int tri_off = -1, int q = 1) {
+  const int kk = min(k + M, b);
+  const int t = threadIdx.x;
+  // Wide factors: warp 0 forms reflector j (column norm, then the square root / reciprocal
+  // chain) while the other warps apply the scaling still owed by the stored column of
+  // reflector pj (rows pr0..pM-1) and already take the dot products of reflector j's
+  // unscaled column with the trailing columns (the scalars are needed only when w is
+  // formed).
+  const int nth = NT - 32;
+  int pj = -1, pr0 = 0, pM = 0;
+  T pend = T(1);
+  auto dots = [&](int u, int j, int r0, int Mj, int nc, int G) {
+    if (nc > 0 && u < G * nc) {
+      const int g = u / nc, c = u - g * nc;
+      const T *X = tile + j + 1 + c;
+      if constexpr (is_df<T>::value) {
+        float sh = 0.f, sl = 0.f;
+        for (int r = r0 + g; r < Mj; r += G) df_dot_acc(sh, sl, tile[(size_t)r * ldt + j], X[(size_t)r * ldt]);
+        s.red[g * nc + c] = df_finish(sh, sl);
+      } else {
+        T acc = T(0);
+        for (int r = r0 + g; r < Mj; r += G) acc += tile[(size_t)r * ldt + j] * X[(size_t)r * ldt];
+        s.red[g * nc + c] = acc;
+      }
+    }
+  };
+  for (int j = 0; j < kk; ++j) {
+    const int r0 = j < k ? 0 : j - k + 1;
+    const int Mj = tile_rows_for(j, M, tri_off, q);
+    T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
+    const int nc = b - j - 1, nrow = Mj - r0;
+    // dot-product groups over the nth threads taking them (nc < b <= TT_MAX_RANK < NT - 32)
+    int G = nc > 0 ? nth / nc : 1;
+    if (G > nrow) G = nrow > 0 ? nrow : 1;
+    if (t < 32) {
+      T ss = T(0);
+      for (int r = r0 + t; r < Mj; r += 32) {
+        const T v = tile[(size_t)r * ldt + j];
+        ss += v * v;
+      }
+      ss = warp_sum(ss);
+      if (t == 0) {
+        T tj = T(0), scale = T(0);
+        if (ss != T(0)) {
+          const T alpha = piv[j];
+          const T v = alpha * alpha + ss;
+          const bool fast = std::is_same<T, double>::value && nr_range((double)v);
+          const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
+          const T beta = alpha >= T(0) ? -nrm : nrm;
+          const T d = alpha - beta;
+          const T bd = beta * d;
+          if (fast && nr_range(fabs((double)bd))) {
+            // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q
+            // and 1 / d = beta q
+            const T qq = (T)rcp_nr((double)bd);
+            tj = -d * d * qq;
+            scale = beta * qq;
+          } else {
+            // textbook form; tau lies in [1, 2] whatever the scale of the column
+            tj = (beta - alpha) / beta;
+            scale = T(1) / d;
+          }
+          piv[j] = beta;
+        }
+        tau[j] = tj;
+        s.sc[0] = scale;
+        s.sc[1] = tj;
+      }
+    } else {
+      const int u = t - 32;
+      if (pj >= 0)
+        for (int r = pr0 + u; r < pM; r += NT - 32) tile[(size_t)r * ldt + pj] *= pend;
+      dots(u, j, r0, Mj, nc, G);
+    }
+    __syncthreads();
+    const T tj = s.sc[1];
+    pj = -1;
+    if (tj != T(0)) {
+      const T scale = s.sc[0];
+      if (nc > 0) {
+        for (int h = G; h > 1;) {
+          const int half = (h + 1) >> 1;
+          for (int idx = t; idx < (h - half) * nc; idx += NT) s.red[idx] += s.red[idx + half * nc];
+          h = half;
+          __syncthreads();
+        }
+        T *p = piv + j + 1;
+        if (t < nc) {
+          const T w = tj * (p[t] + scale * s.red[t]);
+          s.wbuf[t] = scale * w;
+          p[t] -= w;
+        }
+        __syncthreads();
+        if (nrow > 0) {
+          // dense walk over the nrow x nc trailing block: X -= v w^T (v unscaled, w scaled)
+          const int dq = NT / nc, dr = NT - dq * nc;
+          int r = t / nc, cc = t - (t / nc) * nc;
+          for (; r < nrow;) {
+            const size_t rr = (size_t)(r0 + r);
+            if constexpr (is_df<T>::value) {
+              T &x = tile[rr * ldt + j + 1 + cc];
+              x = df_sub_prod(x, tile[rr * ldt + j], s.wbuf[cc]);
+            } else {
+              tile[rr * ldt + j + 1 + cc] -= tile[rr * ldt + j] * s.wbuf[cc];
+            }
+            r += dq;
+            cc += dr;
+            if (cc >= nc) {
+              cc -= nc;
+              ++r;
+            }
+          }
+        }
+      }
+      pj = j;
+      pend = scale;
+      pr0 = r0;
+      pM = Mj;
+    }
+    __syncthreads();
+  }
+  if (pj >= 0) {
+    for (int r = pr0 + t; r < pM; r += NT) tile[(size_t)r * ldt + pj] *= pend;
+  }
+  __syncthreads();
+  return kk;
+}
+
+// Householder QR of the stacked matrix (see above).  Factors of 48 or more columns take
+// reflector j's dot products while its scalars are being formed (hh_factor_ahead); narrower
+// ones measured faster with all threads on the dot products after the scalars
+// (hh_factor_seq), as that spreads fewer products per reflector over more threads.
+template <typename T>
+__device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+                         int tri_off = -1, int q = 1) {
+  return b >= 48 ? hh_factor_ahead(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q)
+                 : hh_factor_seq(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q);
 }
 
 // Moves the new R rows k..kk-1 produced by hh_factor from the tile into Rr (zeroing the

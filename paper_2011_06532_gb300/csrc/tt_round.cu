@@ -346,7 +346,11 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
   // CT lives right after V (MT x ncol)
   const int q = blockIdx.x, t = threadIdx.x, b = a.b;
   const int rho = dyn(a.rho_dyn, a.rho);
-  const int nc = dyn(a.ncol_dyn, a.ncol);
+  // the columns of C are independent under Q: CTA y of the node takes columns [cb, cb + nc)
+  const int ncol = dyn(a.ncol_dyn, a.ncol);
+  const int chunk = (ncol + gridDim.y - 1) / gridDim.y;
+  const int cb = blockIdx.y * chunk, nc = min(ncol, cb + chunk) - cb;
+  if (nc <= 0) return;
   double *CT = V + (size_t)a.MT * a.lda;
   const int c0 = q * a.G, c1 = min(a.nchild, c0 + a.G);
   // replay the k sequence of the factorization
@@ -361,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
     }
   }
   // load node C (k rows)
-  const double *Cn = a.Cin + (size_t)q * b * a.ldc;
+  const double *Cn = a.Cin + (size_t)q * b * a.ldc + cb;
   for (int idx = t; idx < b * nc; idx += NT) {
     const int r = idx / nc, col = idx - r * nc;
     C[r * nc + col] = r < k ? Cn[(size_t)r * a.ldc + col] : 0.0;
@@ -383,9 +387,9 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
     for (int idx = t; idx < M * nc; idx += NT) {
       const int row = idx / nc, col = idx - row * nc;
       const int r = row / qq, i = row - r * qq;
-      a.Cout[(size_t)(c0 + 1 + i) * b * a.ldc + (size_t)r * a.ldc + col] = CT[idx];
+      a.Cout[(size_t)(c0 + 1 + i) * b * a.ldc + (size_t)r * a.ldc + cb + col] = CT[idx];
     }
-    double *Cc0 = a.Cout + (size_t)c0 * b * a.ldc;
+    double *Cc0 = a.Cout + (size_t)c0 * b * a.ldc + cb;
     for (int idx = t; idx < b * nc; idx += NT) {
       const int r = idx / nc, col = idx - r * nc;
       Cc0[(size_t)r * a.ldc + col] = C[r * nc + col];
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
   for (int c = c1 - 1; c > c0; --c) {
     const int kc = child_rows_k(a, c, rho);
     const double *slot = a.slots + (size_t)c * (b * b + a.nchunk * b);
-    double *Cc = a.Cout + (size_t)c * b * a.ldc;
+    double *Cc = a.Cout + (size_t)c * b * a.ldc + cb;
     const int nch = (kc + a.MT - 1) / a.MT;
     for (int ch = nch - 1; ch >= 0; --ch) {
       const int ra = ch * a.MT, M = min(a.MT, kc - ra);
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(NT) k_tree_apply(TreeArgs a) {
   }
   // first child keeps the remaining rows
   const int k0 = child_rows_k(a, c0, rho);
-  double *Cc = a.Cout + (size_t)c0 * b * a.ldc;
+  double *Cc = a.Cout + (size_t)c0 * b * a.ldc + cb;
   for (int idx = t; idx < k0 * nc; idx += NT) {
     const int r = idx / nc, col = idx - r * nc;
     Cc[(size_t)r * a.ldc + col] = C[r * nc + col];
@@ -1508,6 +1512,7 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
 // root-to-leaves application; the root C sits at Cbase level nlev; leaf C's end at level 0
 static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, int ncol, const int *ncol_dyn,
                       int cmax, double *Cbase, const double *slots, int B, cudaStream_t st) {
+  const int pl_nsm = device_sm_count();
   const SmemTree sm = smem_tree(b, cmax, tr.G);
   const SmemTree smf = smem_tree(b, b, tr.G);  // the slots hold the factorization's chunking
   SmemTree use = sm;
@@ -1551,9 +1556,12 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
     a.oW = use.oW;
     a.oSc = use.oSc;
     a.oTau = use.oTau;
+    // one CTA per node, and the columns of C split over more CTAs while the level has
+    // fewer nodes than SMs (at least 8 columns each)
+    const int ny = std::max(1, std::min((pl_nsm + tr.count[l + 1] - 1) / tr.count[l + 1], (cmax + 7) / 8));
     {
       TraceScope ts_(TT_K_TREE_APPLY, st);
-      k_tree_apply<<<tr.count[l], NT, use.bytes, st>>>(a);
+      k_tree_apply<<<dim3(tr.count[l + 1], ny), NT, use.bytes, st>>>(a);
     }
     TT_CUDA(cudaGetLastError());
   }
