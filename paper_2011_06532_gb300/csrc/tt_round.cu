@@ -676,8 +676,13 @@ __device__ __forceinline__ T seg_sum(T v) {
 // Each pair is handled by a segment of LP = 8 lanes (4 pairs per warp): on GB300 an FP64
 // warp instruction costs the FP64 unit the same time whatever its active lanes, so the
 // per-pair dot products, reductions and rotation angle are packed four to an instruction.
+// quad_stop: also stop after a sweep whose largest rotated cos^2 = ga^2 / (al be) is at
+// most 0.1 tol: cyclic Jacobi converges quadratically (the next sweep's cos^2 is about the
+// square of this one's), so the sweep that would only confirm convergence is skipped.
+// pos holds 2 * (ns + 2) ints, flag 2 ints.
 template <typename T>
-__device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2) {
+__device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2,
+                       bool quad_stop = false) {
   constexpr int LP = 8, PW = 32 / LP;  // lanes per pair, pairs per warp
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   const int seg = lane / LP, sl = lane - seg * LP;
@@ -689,7 +694,10 @@ __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, i
   int cur = 0;
   const T tol2 = tol * tol;
   for (int sweep = 0; sweep < maxsweeps; ++sweep) {
-    if (t == 0) flag[0] = 0;
+    if (t == 0) {
+      flag[0] = 0;
+      flag[1] = 0;  // bits of the largest rotated cos^2 (a non-negative float orders as an int)
+    }
     __syncthreads();
     for (int round = 0; round < n2 - 1; ++round) {
       const int *P = pos + cur * stride;
@@ -718,6 +726,7 @@ __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, i
         be = seg_sum<LP>(be);
         ga = seg_sum<LP>(ga);
         if (!live || ga == T(0) || ga * ga <= tol2 * al * be || (al <= neg2 && be <= neg2)) continue;
+        if (quad_stop && sl == 0) atomicMax(flag + 1, __float_as_int((float)((ga / al) * (ga / be))));
         T cs, sn;
         jrot(al, be, ga, cs, sn);
         for (int r = sl; r < ms; r += LP) {
@@ -740,8 +749,10 @@ __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, i
       __syncthreads();
     }
     const int any = flag[0];
+    const float cmax = __int_as_float(flag[1]);
     __syncthreads();
     if (!any) return true;
+    if (quad_stop && (double)cmax <= 0.1 * (double)tol) return true;
   }
   return false;
 }
@@ -872,7 +883,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   }
   const double neg2 = sig[0];
   __syncthreads();
-  const bool converged = jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2);
+  const bool converged = jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, true);
   // singular values
   const int lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   for (int c = warp; c < ns; c += nwarp) {
