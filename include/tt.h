@@ -55,7 +55,8 @@ typedef enum {
   TT_ERR_WORKSPACE = 2,   /* workspace missing or smaller than the size query returned */
   TT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   TT_ERR_NUMERICAL = 4,   /* non-finite values met, or an SVD did not converge */
-  TT_ERR_UNSUPPORTED = 6  /* a rank above TT_MAX_RANK */
+  TT_ERR_UNSUPPORTED = 6  /* a rank whose buffers the planner cannot place (above 117
+                             for 3-D cores; every rank above TT_MAX_RANK) */
 } tt_status;
 
 typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
