@@ -50,6 +50,31 @@ def parse_args():
     return p.parse_args()
 
 
+# --------------------------------------------------------------------------------------
+# multi-rank plumbing (one process per GPU; the ranks share no data, only the clock)
+# --------------------------------------------------------------------------------------
+
+def rank_seed(rank):
+    """Seed of rank r's independent TT (rank 0 rounds the single-GPU workload)."""
+    return SEED + 7919 * rank
+
+
+def max_over_ranks(x, dist, device):
+    """Largest x over the ranks (the job's time is its slowest rank's); x itself without dist."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, ms):
+    """Whole-job rounds per second: every rank rounded `steps` TTs in the slowest rank's ms."""
+    return world * steps / (ms / 1e3)
+
+
 def workload_desc(I):
     return (f"plain-FP64 TT rounding, N={N_MODES}, I_n={I}, X = Y + (0.5Y + 1e-9Z) with rank-{RANK} Y, Z "
             f"(formal ranks {2 * RANK}), eps={EPS:g}")
@@ -454,7 +479,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     ttgb.build()
     dev = torch.device("cuda", local)
-    seed = SEED + 7919 * rank
+    seed = rank_seed(rank)
     I = [args.modes] * N_MODES
     Y, Yp = ttgen.perturbed_pair(I, RANK, seed)
     dY = ttgb.from_host(Y.I, Y.R, Y.cores, device=dev)
@@ -486,13 +511,9 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     ttgb.trace(False)
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     clk = clocks.stop()
     tr = ttgb.trace_read()
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     launches = sum(v[0] for v in tr.values())
     out_bytes = out.nbytes()
 
@@ -515,11 +536,7 @@ def run_ours(args):
         d2h += sum(c.numel() * 8 for c in y.cores)
     e3.record(stream)
     barrier()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist, dev)
     dX = [torch.empty_like(c) for c in X.cores]
     barrier()
     e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -532,18 +549,14 @@ def run_ours(args):
             hOut[k][: c.numel()].copy_(c, non_blocking=True)
     e5.record(stream)
     barrier()
-    ms_copy = e4.elapsed_time(e5)
-    if dist is not None:
-        t = torch.tensor([ms_copy], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_copy = float(t.item())
+    ms_copy = max_over_ranks(e4.elapsed_time(e5), dist, dev)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
-    rounds_per_s = world * args.steps / (ms / 1e3)
+    rounds_per_s = job_rate(world, args.steps, ms)
     fl = flops_by_kernel(I, X.R, L)
     dom = max(("s1_leaf", "s2_leaf", "s2_out"), key=lambda k: tr[k][1])
     n_dom, ms_dom = tr[dom]
@@ -583,10 +596,10 @@ def run_ours(args):
                      "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz"},
         "kernel_ms_per_step": {k: v[1] / args.steps for k, v in tr.items() if v[0]},
         "cpu_baseline": cpu,
-        "e2e": {"value": world * args.steps / (ms_e2e / 1e3), "unit": "TT-rounds/s",
+        "e2e": {"value": job_rate(world, args.steps, ms_e2e), "unit": "TT-rounds/s",
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps,
                 "path": "tt_round on pinned host cores (kernels read inputs and write outputs over the host link)",
-                "staged_copies": {"value": world * args.steps / (ms_copy / 1e3), "unit": "TT-rounds/s",
+                "staged_copies": {"value": job_rate(world, args.steps, ms_copy), "unit": "TT-rounds/s",
                                   "path": "host->device copies, device tt_round, device->host copies"}},
         "gpu_launches": launches,
         "clocks": clk,
