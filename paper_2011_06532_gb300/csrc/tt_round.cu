@@ -1172,45 +1172,69 @@ SmemOut<T> smem_out(int K1, int Lmax, int Tt, bool spill = false) {
 
 struct SmemTree {
   int oA, oB, oRed, oW, oSc, oTau, lda, MT, nchunk;
+  int w = 0;  // columns of C per CTA (apply layouts)
   size_t bytes;
 };
 
-// factor: A = Rr (b x b), B = tile (MT x lda); apply: A = C (b x cmax), B = V (MT x lda) + CT (MT x cmax).
-// The tile takes (G - 1) b rows (a node's other triangles at once) when that fits, else
-// b rows, else the largest halving of b that fits (a child in chunks).
-SmemTree smem_tree(int b, int cmax, int G) {
-  SmemTree m;
-  m.lda = b + 1;
-  for (m.MT = std::max(1, G - 1) * b; m.MT > 1; m.MT = m.MT > b ? b : (m.MT + 1) / 2) {
-    Carve c;
-    size_t A = std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double);
-    size_t B = ((size_t)m.MT * m.lda + (size_t)m.MT * cmax) * sizeof(double);
-    c.take(A);
-    c.take(B);
-    c.take(sizeof(double) * NT);
-    c.take(sizeof(double) * std::max(b, cmax));
-    c.take(sizeof(double) * 2);
-    c.take(sizeof(double) * b);
-    if (c.off <= kSmemBudget) break;
-  }
+// Shared memory of the tree kernels.  Factor: A = Rr (b x b), B = tile (MT x lda).
+// Apply: A = C (b x w), B = V (MT x lda) + CT (MT x w), w = the columns of C one CTA takes.
+// MT = tile rows: (G - 1) b (a node's other triangles at once) when that fits, else b,
+// else the largest halving of b that fits (a child in chunks); the apply must fit with
+// the factor's MT (the slots hold its chunking) and at least kTreeMinCols columns.
+constexpr int kTreeMinCols = 8;
+
+static size_t tree_bytes(int b, int MT, int w, SmemTree *m) {
   Carve c;
-  m.oA = (int)c.take(std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double));
-  m.oB = (int)c.take(((size_t)m.MT * m.lda + (size_t)m.MT * cmax) * sizeof(double));
-  m.oRed = (int)c.take(sizeof(double) * NT);
-  m.oW = (int)c.take(sizeof(double) * std::max(b, cmax));
-  m.oSc = (int)c.take(sizeof(double) * 2);
-  m.oTau = (int)c.take(sizeof(double) * b);
-  m.bytes = c.off;
-  m.nchunk = (b + m.MT - 1) / m.MT;
+  const int oA = (int)c.take((size_t)b * std::max(b, w) * sizeof(double));
+  const int oB = (int)c.take(((size_t)MT * (b + 1) + (size_t)MT * w) * sizeof(double));
+  const int oRed = (int)c.take(sizeof(double) * NT);
+  const int oW = (int)c.take(sizeof(double) * std::max(b, w));
+  const int oSc = (int)c.take(sizeof(double) * 2);
+  const int oTau = (int)c.take(sizeof(double) * b);
+  if (m) {
+    m->lda = b + 1;
+    m->MT = MT;
+    m->oA = oA;
+    m->oB = oB;
+    m->oRed = oRed;
+    m->oW = oW;
+    m->oSc = oSc;
+    m->oTau = oTau;
+    m->bytes = c.off;
+    m->nchunk = (b + MT - 1) / MT;
+    m->w = w;
+  }
+  return c.off;
+}
+
+// factor layout (w = 0: no CT), MT chosen so that the apply also fits with kTreeMinCols
+SmemTree smem_tree(int b, int G) {
+  int MT = std::max(1, G - 1) * b;
+  for (; MT > 1; MT = MT > b ? b : (MT + 1) / 2)
+    if (tree_bytes(b, MT, 0, nullptr) <= kSmemBudget &&
+        tree_bytes(b, MT, std::min(b, kTreeMinCols), nullptr) <= kSmemBudget)
+      break;
+  SmemTree m;
+  tree_bytes(b, MT, 0, &m);
   return m;
 }
 
-// Tree fan-in for factors of b columns: 4 children per node (one pass of b reflectors
-// over three interleaved triangles: half the serial reflectors of a binary tree from leaves
-// to root) when such a tile fits in shared memory, else 3, else 2.
+// apply layout for the factor's MT: the widest column chunk (<= cmax) that fits
+SmemTree smem_tree_apply(int b, int G, int cmax) {
+  const SmemTree f = smem_tree(b, G);
+  int w = std::max(1, cmax);
+  while (w > 1 && tree_bytes(b, f.MT, w, nullptr) > kSmemBudget) --w;
+  SmemTree m;
+  tree_bytes(b, f.MT, w, &m);
+  return m;
+}
+
+// Tree fan-in for factors of b columns: 4 children per node (one pass of b reflectors over
+// three interleaved triangles: half the serial reflectors of a binary tree from leaves to
+// root) when such a tile fits in shared memory, else 3, else 2.
 int tree_fanin(int b) {
   for (int G : {4, 3}) {
-    const SmemTree m = smem_tree(b, b, G);
+    const SmemTree m = smem_tree(b, G);
     if (m.bytes <= kSmemBudget && m.MT >= (G - 1) * b) return G;
   }
   return 2;
@@ -1389,7 +1413,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
   for (int n = 0; n + 1 < N && !sweep1_only; ++n)
     if (smem_svd(pl.core[n].K1, false) > kSmemBudget) return TT_ERR_UNSUPPORTED;
   for (int n = 1; n < N; ++n)
-    if (smem_tree(pl.core[n].R0, pl.core[n].R0, pl.core[n].tree.G).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
+    if (smem_tree(pl.core[n].R0, pl.core[n].tree.G).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
   // workspace layout
   Carve w;
   pl.off_L = w.take(sizeof(int) * (N + 1), 256);
@@ -1405,7 +1429,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
     if (n >= 1 && pl.keep_q) {
       c.refl_off = w.take(sizeof(T) * (size_t)c.I * c.K1 * c.R0, 256);
       c.tau_off = w.take(sizeof(T) * (size_t)c.I * c.R0, 256);
-      const SmemTree st = smem_tree(c.R0, c.R0, c.tree.G);
+      const SmemTree st = smem_tree(c.R0, c.tree.G);
       c.slot_off = w.take(sizeof(double) * c.tree.nslots * ((size_t)c.R0 * c.R0 + (size_t)st.nchunk * c.R0), 256);
     }
     if (n < N - 1) {
@@ -1486,7 +1510,7 @@ static int set_smem(K kernel, size_t bytes) {
 // level-by-level tree factorization of the leaf R's in Rbuf level 0; root ends at level nlev
 static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, double *Rbase, double *slots,
                        int B, cudaStream_t st) {
-  const SmemTree sm = smem_tree(b, b, tr.G);  // same chunking as the apply (at most b columns)
+  const SmemTree sm = smem_tree(b, tr.G);  // the apply replays this chunking
   int r = set_smem(k_tree_factor, sm.bytes);
   if (r) return r;
   for (int l = 0; l < tr.nlev; ++l) {
@@ -1524,22 +1548,11 @@ static int tree_factor(const Tree &tr, int b, int64_t I, int rho, const int *rho
 static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_dyn, int ncol, const int *ncol_dyn,
                       int cmax, double *Cbase, const double *slots, int B, cudaStream_t st) {
   const int pl_nsm = device_sm_count();
-  const SmemTree sm = smem_tree(b, cmax, tr.G);
-  const SmemTree smf = smem_tree(b, b, tr.G);  // the slots hold the factorization's chunking
-  SmemTree use = sm;
-  use.MT = smf.MT;
-  use.nchunk = smf.nchunk;
-  {
-    Carve c;
-    use.oA = (int)c.take(std::max((size_t)b * b, (size_t)b * cmax) * sizeof(double));
-    use.oB = (int)c.take(((size_t)use.MT * use.lda + (size_t)use.MT * cmax) * sizeof(double));
-    use.oRed = (int)c.take(sizeof(double) * NT);
-    use.oW = (int)c.take(sizeof(double) * std::max(b, cmax));
-    use.oSc = (int)c.take(sizeof(double) * 2);
-    use.oTau = (int)c.take(sizeof(double) * b);
-    use.bytes = c.off;
-  }
-  if (use.bytes > kSmemBudget || tr.G * use.nchunk > 64) return TT_ERR_UNSUPPORTED;
+  // the factorization's tile rows (its chunking is in the slots), and the widest column
+  // chunk of C one CTA can take next to them
+  const SmemTree use = smem_tree_apply(b, tr.G, cmax);
+  const int wmax = use.w;
+  if (use.bytes > kSmemBudget || tr.G * use.nchunk > 64 || wmax < 1) return TT_ERR_UNSUPPORTED;
   int r = set_smem(k_tree_apply, use.bytes);
   if (r) return r;
   for (int l = tr.nlev - 1; l >= 0; --l) {
@@ -1567,9 +1580,10 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
     a.oW = use.oW;
     a.oSc = use.oSc;
     a.oTau = use.oTau;
-    // one CTA per node, and the columns of C split over more CTAs while the level has
-    // fewer nodes than SMs (at least 8 columns each)
-    const int ny = std::max(1, std::min((pl_nsm + tr.count[l + 1] - 1) / tr.count[l + 1], (cmax + 7) / 8));
+    // one CTA per node, the columns of C split over more CTAs while the level has fewer
+    // nodes than SMs (at least 8 columns each), and always into chunks of at most wmax
+    const int ny = std::max((cmax + wmax - 1) / wmax,
+                            std::max(1, std::min((pl_nsm + tr.count[l + 1] - 1) / tr.count[l + 1], (cmax + 7) / 8)));
     {
       TraceScope ts_(TT_K_TREE_APPLY, st);
       k_tree_apply<<<dim3(tr.count[l + 1], ny), NT, use.bytes, st>>>(a);

@@ -1,8 +1,8 @@
 """GPU parity of the TSQR tree shapes: nodes that factor their children's triangles in one
-interleaved pass (fan-in 4 up to rank 48, 3 up to 64), nodes that take short children one
-by one (leaves holding fewer rows than the rank), binary trees at ranks above 64 (up to
-117, the largest rank whose buffers the planner can place), and applies split over column
-chunks at the upper levels -- each against the oracle (ranks
+interleaved pass (fan-in 4 up to rank 79, 3 up to 93), nodes that take short children one
+by one (leaves holding fewer rows than the rank), binary trees at higher ranks (up to 117,
+the largest rank whose buffers the planner can place), and applies split over column
+chunks -- each against the oracle (ranks
 identical, relative error <= 1e-12 in FP64, <= 1e-6 in fp32x2)."""
 import pytest
 
@@ -33,8 +33,8 @@ CASES = [
     # (I, R, eps): what the shape exercises
     ([64, 50, 64], [1, 32, 8, 1], 1e-6),          # 50 one-slice leaves of 8 rows < 32: short children, then full ones
     ([3000, 2500, 3000], [1, 24, 24, 1], 1e-6),   # fan-in 4, interleaved nodes at every level
-    ([2000, 1800, 2000], [1, 60, 60, 1], 1e-6),   # fan-in 3 (rank 60)
-    ([900, 700, 900], [1, 80, 80, 1], 1e-6),      # rank 80: binary tree, chunked node tiles
+    ([2000, 1800, 2000], [1, 60, 60, 1], 1e-6),   # fan-in 4 at rank 60
+    ([900, 700, 900], [1, 80, 80, 1], 1e-6),      # fan-in 3 at rank 80, apply in column chunks
     ([5000, 37, 5000], [1, 40, 40, 1], 0.0),      # wide middle core (37 slices of 40 rows), eps = 0
     ([300, 260, 300], [1, 100, 100, 1], 1e-6),    # rank 100: leaf buffers spilled to the global scratch
     ([240, 200, 240], [1, 117, 117, 1], 1e-6),    # the largest rank the planner accepts
