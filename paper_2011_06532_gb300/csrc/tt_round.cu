@@ -54,6 +54,8 @@ struct S1Args {
   int ldt;
   T *gscr;
   size_t gstride;
+  const float2 *Pm32;  // Pm split into FP32 pairs (hi, lo), for the FP32-storage types
+  int stage_p;         // FP32-storage types: 1 = stage Pm32 in shared memory (oPs), 0 = read it via L1
 };
 
 struct TreeArgs {
@@ -168,6 +170,14 @@ __device__ __forceinline__ int64_t rows_of_leaves(int64_t I, int P, int l0, int 
 // sweep 1 leaf: push + sequential Householder over tiles
 // ------------------------------------------------------------------------------------
 
+// an entry of the pushed factor in the compute type
+__device__ __forceinline__ double load_pm(const double *P, int i, double) { return P[i]; }
+__device__ __forceinline__ df32 load_pm(const float2 *P, int i, df32) {
+  const float2 v = P[i];
+  return df32(v.x, v.y);
+}
+__device__ __forceinline__ float load_pm(const float2 *P, int i, float) { return P[i].x; }
+
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -179,11 +189,12 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
   const int b = a.b, rho = a.rho, cin = a.cin, ldt = a.ldt;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
   const bool push = a.Pm != nullptr;
-  // FP64 reads the pushed factor through L1 (no conversion needed, and the shared memory
-  // it would take lets more leaf CTAs share an SM); other compute types stage a converted copy
+  // The pushed factor: FP64 reads it through L1 as is.  The FP32-storage types stage its
+  // (hi, lo) split in shared memory when two leaf CTAs still fit on an SM with it, and
+  // read the split through L1 otherwise (the staged copy would halve the resident CTAs).
   constexpr bool stage = !std::is_same<T, double>::value;
-  if (push && stage)
-    for (int idx = t; idx < rho * cin; idx += NT) Ps[idx] = (T)a.Pm[idx];
+  if (push && stage && a.stage_p)
+    for (int idx = t; idx < rho * cin; idx += NT) Ps[idx] = load_pm(a.Pm32, idx, T());
   for (int idx = t; idx < b * b; idx += NT) Rr[idx] = T(0);
   __syncthreads();
   int k = 0;
@@ -210,8 +221,8 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
           Xs[idx] = T(a.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem]);
         }
         __syncthreads();
-        // two copies of the loop so that the staged factor is addressed as shared memory
-        // whenever it lives there
+        // one copy of the loop per place the factor is read from (FP64 global, staged
+        // shared copy, or the (hi, lo) split in global memory)
         auto push_tile = [&](const T *P) {
           for (int idx = t; idx < M * b; idx += NT) {
             const int r = idx / b, col = idx - r * b;
@@ -228,12 +239,34 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
             tile[r * ldt + col] = acc;
           }
         };
-        if constexpr (!stage)
+        if constexpr (!stage) {
           push_tile(reinterpret_cast<const T *>(a.Pm));
-        else if (a.oPs >= 0)
-          push_tile(sm<T>(smem, a.oPs));
-        else
-          push_tile(Ps);
+        } else {
+          auto push_split = [&](const float2 *P) {
+            for (int idx = t; idx < M * b; idx += NT) {
+              const int r = idx / b, col = idx - r * b;
+              const int sl = r / rho, kr = r - sl * rho;
+              T acc = tile[r * ldt + col];
+              const int cstart = max(kr, c0);
+              if constexpr (is_df<T>::value) {
+                float ah = acc.hi, al = acc.lo;
+                for (int c = cstart; c < c0 + cc_n; ++c)
+                  df_dot_acc(ah, al, load_pm(P, kr * cin + c, T()), Xs[((c - c0) * nt + sl) * b + col]);
+                acc = df_finish(ah, al);
+              } else {
+                for (int c = cstart; c < c0 + cc_n; ++c)
+                  acc += load_pm(P, kr * cin + c, T()) * Xs[((c - c0) * nt + sl) * b + col];
+              }
+              tile[r * ldt + col] = acc;
+            }
+          };
+          if (!a.stage_p)
+            push_split(a.Pm32);
+          else if (a.oPs >= 0)
+            push_tile(sm<T>(smem, a.oPs));
+          else
+            push_tile(Ps);
+        }
       }
     }
     __syncthreads();
@@ -994,10 +1027,16 @@ __global__ void k_sum_sqrt(const double *partial, int n, const int *E, double *o
 
 // Moves the root factor of sweep 1 (n entries) to the pushed-factor region, dividing it by
 // 2^e when its largest entry leaves [2^-32, 2^32] and adding e to E.
-__global__ void __launch_bounds__(256) k_take_root(const double *root, int n, double *keep, int *E) {
+// Also writes the factor split into FP32 pairs (hi, lo) for the FP32-storage leaves.
+__global__ void __launch_bounds__(256) k_take_root(const double *root, int n, double *keep, float2 *keep32, int *E) {
   __shared__ double red[8];
   const int e = range_exp(block_absmax(root, n, red));
-  for (int i = threadIdx.x; i < n; i += blockDim.x) keep[i] = ldexp(root[i], -e);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = ldexp(root[i], -e);
+    keep[i] = v;
+    const float hi = (float)v;
+    keep32[i] = make_float2(hi, (float)(v - (double)hi));
+  }
   if (threadIdx.x == 0 && e != 0) *E += e;
 }
 
@@ -1094,7 +1133,7 @@ struct SmemS1 {
 };
 
 template <typename T>
-SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false) {
+SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false, bool stage_p = false) {
   SmemS1<T> m;
   Place pl{Carve(), spill};
   Carve &c = pl.c;
@@ -1102,8 +1141,10 @@ SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false) {
   m.oRr = pl.take(sizeof(T) * b * b, (size_t)b * b, true);
   m.oTile = (int)c.take(sizeof(T) * (size_t)Tt * rho * m.ldt);
   m.oXs = (int)c.take(sizeof(T) * (size_t)CC * Tt * b);
-  m.oPs = std::is_same<T, double>::value ? (int)c.take(16)
-                                          : pl.take(sizeof(T) * (size_t)rho * cin, (size_t)rho * cin, true);
+  // the pushed factor's staged copy (FP32-storage types only, see k_s1_leaf)
+  m.oPs = stage_p && !std::is_same<T, double>::value
+              ? pl.take(sizeof(T) * (size_t)rho * cin, (size_t)rho * cin, true)
+              : (int)c.take(16);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(b, 1));
   m.oSc = (int)c.take(sizeof(T) * 2);
@@ -1281,7 +1322,7 @@ struct RoundPlan {
   int bmax = 1;  // max input rank
   std::vector<CorePlan> core;
   // workspace layout (bytes)
-  size_t off_ctl = 0, off_L = 0, off_scal = 0, off_status = 0, off_P = 0;
+  size_t off_ctl = 0, off_L = 0, off_scal = 0, off_status = 0, off_P = 0, off_P32 = 0;
   size_t off_R = 0, off_C1 = 0, off_C2 = 0, off_slots2 = 0, off_refl2 = 0, off_tau2 = 0, off_part = 0;
   size_t max_nodes = 0, max_slots = 0;
   size_t total = 0;
@@ -1306,7 +1347,7 @@ static size_t core_smem(const RoundPlan &pl, int n, int Tt, bool spill, bool swe
     g = std::max(g, gs);
   };
   if (n >= 1) {
-    const SmemS1<T> a = smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC, spill);
+    const SmemS1<T> a = smem_s1<T>(c.R0, c.K1, c.R1, Tt, CC, spill, true);
     acc(a.bytes, a.gstride);
     if (!sweep1_only) {
       if (n < N - 1) {
@@ -1420,6 +1461,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
   pl.off_scal = w.take(sizeof(double) * 4, 256);
   pl.off_status = w.take(sizeof(int) * 4, 256);
   pl.off_P = w.take(sizeof(double) * (size_t)pl.bmax * pl.bmax, 256);
+  pl.off_P32 = w.take(sizeof(float2) * (size_t)pl.bmax * pl.bmax, 256);
   size_t max_nodes = 1, max_slots = 1, max_refl2 = 1, max_tau2 = 1;
   const size_t B = (size_t)pl.bmax;
   for (int n = 0; n < N; ++n) {
@@ -1601,7 +1643,10 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
   const double *Pm = nullptr;  // root R of the previous core (device), K_{n+1} x R_{n+1}
   for (int n = N - 1; n >= 1; --n) {
     const CorePlan &c = pl.core[n];
-    const SmemS1<T> m = smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8, c.spill);
+    // FP32-storage types stage the pushed factor only while two leaf CTAs still fit on an SM
+    const bool stage = !std::is_same<T, double>::value && !c.spill &&
+                       smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8, false, true).bytes <= kSmemPair;
+    const SmemS1<T> m = smem_s1<T>(c.R0, c.K1, c.R1, c.Tt, 8, c.spill, stage);
     S1Args<S, T> a{};
     a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
     a.gstride = m.gstride;
@@ -1611,6 +1656,8 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     a.cin = c.R1;
     a.rho = c.K1;
     a.Pm = Pm;
+    a.Pm32 = Pm ? reinterpret_cast<const float2 *>(ws + pl.off_P32) : nullptr;
+    a.stage_p = stage ? 1 : 0;
     a.refl = pl.keep_q ? reinterpret_cast<T *>(ws + c.refl_off) : nullptr;
     a.tau = pl.keep_q ? reinterpret_cast<T *>(ws + c.tau_off) : nullptr;
     a.Rleaf = Rbase + c.tree.node_off[0] * B * B;
@@ -1638,10 +1685,11 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     // can overwrite the tree levels
     double *root = Rbase + c.tree.node_off[c.tree.nlev] * B * B;
     double *keep = reinterpret_cast<double *>(ws + pl.off_P);
+    float2 *keep32 = reinterpret_cast<float2 *>(ws + pl.off_P32);
     // root is b x b row-major with K0 valid rows; the push needs K0 x R0 with ld R0 == b
     {
       TraceScope ts_(TT_K_MISC, st);
-      k_take_root<<<1, 256, 0, st>>>(root, c.R0 * c.R0, keep, E);
+      k_take_root<<<1, 256, 0, st>>>(root, c.R0 * c.R0, keep, keep32, E);
     }
     TT_CUDA(cudaGetLastError());
     Pm = keep;
