@@ -112,3 +112,24 @@ def test_workspace_size_query_has_no_device_side_effects(lib):
     x32 = make_desc([64, 32, 16], [1, 8, 4, 1], dtype=1)
     for prec in [0, 2, 3]:
         assert lib.tt_round_workspace_size(ctypes.byref(x32), prec, ctypes.byref(n)) == 0 and n.value > 0
+
+
+def test_plain_c_client(lib, tmp_path):
+    """The header compiles as C and the library links into a C program (host-only calls)."""
+    import shutil
+    import subprocess
+
+    from paper_2011_06532_gb300 import _native
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = tmp_path / "abi_check"
+    libdir = os.path.dirname(_native.LIB)
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "abi_check.c"), "-o", str(exe), "-L", libdir, "-lttgb",
+                        "-Wl,-rpath," + libdir], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr
+
