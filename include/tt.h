@@ -77,9 +77,11 @@ typedef struct {
   const int64_t *I;     /* host array [N], mode sizes, each >= 1 */
   int64_t *R;           /* host array [N+1], ranks, R[0] = R[N] = 1, each >= 1;
                            written by routines that produce this tensor */
-  void *const *cores;   /* host array [N] of device pointers (tt_round also takes
-                           mapped page-locked host memory), core n holds
-                           R[n] * I[n] * R[n+1] elements of dtype */
+  void *const *cores;   /* host array [N] of pointers the current device can
+                           dereference (its own memory, managed memory, or mapped
+                           page-locked host memory; any other pointer makes a compute
+                           routine return TT_ERR_INVALID_ARG before queueing work),
+                           core n holds R[n] * I[n] * R[n+1] elements of dtype */
 } tt_tensor;
 
 /*

@@ -85,6 +85,11 @@ def _stream(stream: Optional[torch.cuda.Stream]):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _cuda_device(x: DeviceTT) -> torch.device:
+    """The device a call on x runs on (the current one when x's cores are pinned host memory)."""
+    return x.cores[0].device if x.cores[0].is_cuda else torch.device("cuda", torch.cuda.current_device())
+
+
 def _validate(x: DeviceTT, host_ok: bool = False):
     ok = (lambda c: c.is_cuda or (c.device.type == "cpu" and c.is_pinned())) if host_ok else (lambda c: c.is_cuda)
     if not x.cores or any(not ok(c) for c in x.cores):
@@ -128,7 +133,7 @@ def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tens
     if out is not None:
         _validate(DeviceTT(list(x.I), list(x.R), list(out)), host_ok=True)
     lib = _native.load()
-    dev = x.cores[0].device if x.cores[0].is_cuda else torch.device("cuda", torch.cuda.current_device())
+    dev = _cuda_device(x)
     prec = PRECISIONS[precision]
     d = _Desc(x.I, x.R, x.cores, x.dtype)
     n = ctypes.c_size_t(0)
@@ -317,14 +322,14 @@ def tt_hadamard(a: DeviceTT, b: DeviceTT, stream=None) -> DeviceTT:
 
 
 def tt_dot(a: DeviceTT, b: DeviceTT, stream=None) -> float:
-    """Inner product <A, B> (Sec. 3.2.3)."""
-    _validate(a)
-    _validate(b)
+    """Inner product <A, B> (Sec. 3.2.3); cores may be CUDA tensors or pinned host tensors."""
+    _validate(a, host_ok=True)
+    _validate(b, host_ok=True)
     lib = _native.load()
     da, db = _Desc(a.I, a.R, a.cores, a.dtype), _Desc(b.I, b.R, b.cores, b.dtype)
     n = ctypes.c_size_t(0)
     _check(lib.tt_dot_workspace_size(da.ref, db.ref, ctypes.byref(n)), "tt_dot_workspace_size")
-    ws = _workspace(int(n.value), a.cores[0].device)
+    ws = _workspace(int(n.value), _cuda_device(a))
     res = ctypes.c_double(0.0)
     _check(lib.tt_dot(da.ref, db.ref, ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
                       _stream(stream)), "tt_dot")
@@ -332,13 +337,13 @@ def tt_dot(a: DeviceTT, b: DeviceTT, stream=None) -> float:
 
 
 def tt_norm(x: DeviceTT, stream=None) -> float:
-    """Norm through orthonormalization (Sec. 3.2.4)."""
-    _validate(x)
+    """Norm through orthonormalization (Sec. 3.2.4); cores may be CUDA or pinned host tensors."""
+    _validate(x, host_ok=True)
     lib = _native.load()
     d = _Desc(x.I, x.R, x.cores, x.dtype)
     n = ctypes.c_size_t(0)
     _check(lib.tt_norm_workspace_size(d.ref, ctypes.byref(n)), "tt_norm_workspace_size")
-    ws = _workspace(int(n.value), x.cores[0].device)
+    ws = _workspace(int(n.value), _cuda_device(x))
     res = ctypes.c_double(0.0)
     _check(lib.tt_norm(d.ref, ctypes.byref(res), ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
                        _stream(stream)), "tt_norm")

@@ -243,6 +243,7 @@ int check_batch(int32_t count, const tt_tensor *xs, const double *eps, tt_tensor
       return TT_ERR_INVALID_ARG;
     if (resolve_prec(&xs[k], precision) < 0) return TT_ERR_INVALID_ARG;
     if (!ranks_supported(&xs[k])) return TT_ERR_UNSUPPORTED;
+    if (!cores_accessible(&xs[k]) || !cores_accessible(&outs[k])) return TT_ERR_INVALID_ARG;
   }
   return TT_OK;
 }
@@ -356,11 +357,13 @@ int tt_round_batched(int32_t count, const tt_tensor *xs, const double *eps, int 
 
 int tt_add(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, void *stream) {
   if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !valid_out(a, out)) return TT_ERR_INVALID_ARG;
+  if (!cores_accessible(a) || !cores_accessible(b) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
   return ttgb::add_run(a, b, out, as_stream(stream));
 }
 
 int tt_hadamard(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, void *stream) {
   if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !valid_out(a, out)) return TT_ERR_INVALID_ARG;
+  if (!cores_accessible(a) || !cores_accessible(b) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
   return ttgb::hadamard_run(a, b, out, as_stream(stream));
 }
 
@@ -372,11 +375,13 @@ int tt_dot_workspace_size(const tt_tensor *a, const tt_tensor *b, size_t *bytes)
 int tt_dot(const tt_tensor *a, const tt_tensor *b, double *result, void *workspace, size_t workspace_bytes,
            void *stream) {
   if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !result) return TT_ERR_INVALID_ARG;
+  if (!cores_accessible(a) || !cores_accessible(b)) return TT_ERR_INVALID_ARG;
   return ttgb::dot_run(a, b, result, workspace, workspace_bytes, as_stream(stream));
 }
 
 int tt_dot_noalloc(const tt_tensor *a, const tt_tensor *b, double *result, void *stream) {
   if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !result) return TT_ERR_INVALID_ARG;
+  if (!cores_accessible(a) || !cores_accessible(b)) return TT_ERR_INVALID_ARG;
   return ttgb::dot_noalloc_run(a, b, result, as_stream(stream));
 }
 
@@ -389,6 +394,7 @@ int tt_norm_workspace_size(const tt_tensor *x, size_t *bytes) {
 int tt_norm(const tt_tensor *x, double *result, void *workspace, size_t workspace_bytes, void *stream) {
   if (!valid_tensor(x) || !result) return TT_ERR_INVALID_ARG;
   if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (!cores_accessible(x)) return TT_ERR_INVALID_ARG;
   return ttgb::norm_run(x, result, workspace, workspace_bytes, as_stream(stream));
 }
 
