@@ -183,6 +183,30 @@ class ClockSampler:
 # CPU oracle (baseline / reference arm)
 # --------------------------------------------------------------------------------------
 
+def host_cpu():
+    """Model name and logical core count of this host (where the oracle runs)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+
+    return {"model": model or platform.processor() or platform.machine(), "hardware_concurrency": os.cpu_count()}
+
+
 def oracle_sample_time(I_sample, seed):
     import oracle
     import ttgen
@@ -214,7 +238,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(args.modes), "N": N_MODES, "I": args.modes, "formal_rank": 2 * RANK,
                        "eps": EPS, "seed": SEED},
-            "cpu_baseline": {"value": value, "unit": "TT-rounds/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "TT-rounds/s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "TT-rounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -571,7 +596,7 @@ def run_ours(args):
         t_cpu = oracle_sample_time(I_s, SEED)
         cpu = {"value": (I_s / args.modes) / t_cpu, "unit": "TT-rounds/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle tt_round of the same construction with I_n={I_s} ({t_cpu:.1f} s), "
-                         f"scaled by {I_s}/{args.modes} (cost is linear in I_n)"}
+                         f"scaled by {I_s}/{args.modes} (cost is linear in I_n)", "host": host_cpu()}
 
     variants = None
     if world == 1 and args.variants:

@@ -278,7 +278,10 @@ int tt_dot(const tt_tensor *a, const tt_tensor *b, double *result, void *workspa
  * TT_DOT_NOALLOC_SCRATCH_BYTES; two tensors whose ranks are all r fit for
  * r <= 58.
  * The first call on a device looks up that device's scratch address, with the
- * device current; make that first call before any stream capture.  All calls
+ * device current; make that first call before any stream capture.  The address
+ * is kept for the life of the process: after cudaDeviceReset (or anything else
+ * that destroys the device's primary context) it is stale, so do not call this
+ * routine on that device again in the same process.  All calls
  * share the one array and it keeps the last call's contents (every value a call
  * reads it writes first): calls whose work overlaps on the GPU -- other streams,
  * other host threads -- race and give wrong results.  Synchronizes `stream`.

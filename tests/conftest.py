@@ -19,3 +19,25 @@ def orc():
 
     oracle.load()
     return oracle
+
+
+FULL_SIZE_MODULE = "test_gpu_full_size.py"
+
+
+def pytest_collection_finish(session):
+    # the full-size parity tests need minutes of single-threaded oracle work: start it in
+    # spawned worker processes as soon as the run is known to include them
+    if session.config.option.collectonly:
+        return
+    if any(item.nodeid.split("::")[0].endswith(FULL_SIZE_MODULE) for item in session.items):
+        from tests import oracle_pool
+
+        oracle_pool.start()
+
+
+def pytest_sessionfinish(session, exitstatus):
+    import sys as _sys
+
+    mod = _sys.modules.get("tests.oracle_pool")
+    if mod is not None:
+        mod.stop()

@@ -1,0 +1,149 @@
+"""GPU parity against the FP64 CPU oracle at the sizes that are benchmarked.
+
+Every case compares the CUDA path (through the C ABI, in the launch configuration the
+benchmark times: default plans, the library's own tt_add forming the sums) with an
+oracle rounding of the same seeded input, computed in spawned worker processes (see
+oracle_pool.py; one large-mode oracle rounding is ~1.2e11 flops of single-threaded C).
+Ranks must be identical element by element; the error ||Y_gpu - Y_orc|| / ||Y_orc|| is
+measured by the oracle's orthonormalization norm of the difference TT (Sec. 3.2.4) and
+must stay within 1e-12 in FP64 and 1e-6 in the FP32-storage forms (Alg. 2, Ensure
+clause, with the tolerances of the mixed and batched forms).
+
+  * the large-mode workload at full size: N=10, I_n=65536, formal ranks 32 (4.33 GB);
+  * the paper's Model 1 (Sec. 4.2, Table 2): N=50, I_n=2000, Y = 2X - X with X of rank
+    25 (formal ranks 50), in FP64 at eps=1e-8 and fp32x2 at eps=1e-6;
+  * the decaying-spectrum construction at N=50 (formal ranks 64, eps=1e-5) with I_n=2048,
+    in fp32x2 and FP64;
+  * members 0..15, the largest and the smallest of the full-size 512-tensor batched
+    recipe, rounded as one batch in fp32x2 and in FP64.
+
+The FP32-storage inputs are the FP32 roundings of the FP64 tensors the oracle rounds, so
+the reported error includes the input quantisation.
+"""
+import numpy as np
+import pytest
+
+import ttgen
+from tests import oracle_pool
+from ttgen import TT
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+
+    assert torch.cuda.is_available()
+    ttgb.build()
+    return ttgb
+
+
+@pytest.fixture(scope="module")
+def pool():
+    return oracle_pool.get_pool()
+
+
+def down(y) -> TT:
+    import paper_2011_06532_gb300 as ttgb
+
+    return TT(list(y.I), list(y.R), ttgb.to_host(y))
+
+
+def release(gpu):
+    import torch
+
+    gpu._ws_cache.clear()
+    torch.cuda.empty_cache()
+
+
+def as32(gpu, x):
+    return gpu.DeviceTT(list(x.I), list(x.R), [c.float() for c in x.cores])
+
+
+def test_large_modes_full_size_fp64(gpu, pool):
+    Y, Yp = oracle_pool.large_modes_input()
+    X = gpu.tt_add(gpu.from_host(Y.I, Y.R, Y.cores), gpu.from_host(Yp.I, Yp.R, Yp.cores))
+    del Y, Yp
+    got = down(gpu.tt_round(X, oracle_pool.LARGE_MODES["eps"]))
+    del X
+    release(gpu)
+    ref = pool.get("large_modes")
+    assert got.R == ref.R == [1] + [16] * 9 + [1], (got.R, ref.R)
+    err = pool.rel_err_async(got, ref).get(1500)
+    assert err <= TOL64, err
+
+
+def model1_device(gpu, dtype):
+    import torch
+
+    X = oracle_pool.model1_x()
+    dX = gpu.from_host(X.I, X.R, X.cores, dtype=dtype)
+    two = gpu.DeviceTT(list(X.I), list(X.R), [2.0 * dX.cores[0]] + dX.cores[1:])
+    neg = gpu.DeviceTT(list(X.I), list(X.R), [-dX.cores[0]] + dX.cores[1:])
+    return gpu.tt_add(two, neg)
+
+
+@pytest.mark.parametrize("prec,eps,tol", [("fp64", 1e-8, TOL64), ("fp32x2", 1e-6, TOL_MIXED)])
+def test_paper_model1(gpu, pool, prec, eps, tol):
+    import torch
+
+    Y = model1_device(gpu, torch.float64 if prec == "fp64" else torch.float32)
+    got = down(gpu.tt_round(Y, eps, precision=prec))
+    del Y
+    release(gpu)
+    ref = pool.get("model1_%g" % eps)
+    r = oracle_pool.MODEL1["r"]
+    assert got.R == ref.R == ttgen.uniform_ranks(oracle_pool.MODEL1["N"], r), (got.R, ref.R)
+    err = pool.rel_err_async(got, ref).get(1500)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32x2", TOL_MIXED), ("fp64", TOL64)])
+def test_decaying_N50(gpu, pool, prec, tol):
+    terms = oracle_pool.decaying_terms()
+    X = gpu.from_host(terms[0].I, terms[0].R, terms[0].cores)
+    for T in terms[1:]:
+        X = gpu.tt_add(X, gpu.from_host(T.I, T.R, T.cores))
+    del terms
+    if prec != "fp64":
+        X = as32(gpu, X)
+    got = down(gpu.tt_round(X, oracle_pool.DECAYING["eps"], precision=prec))
+    del X
+    release(gpu)
+    ref = pool.get("decaying")
+    assert got.R == ref.R, (got.R, ref.R)
+    assert max(ref.R) < 64  # the threshold cuts the decaying spectra (to ranks near 48)
+    err = pool.rel_err_async(got, ref).get(1500)
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32x2", TOL_MIXED), ("fp64", TOL64)])
+def test_batched_recipe_subset_full_size(gpu, pool, prec, tol):
+    import torch
+
+    members = oracle_pool.batched_subset()
+    xs = []
+    for t in members:
+        (Y, Yp), _ = ttgen.batched_member(t)
+        X = gpu.tt_add(gpu.from_host(Y.I, Y.R, Y.cores), gpu.from_host(Yp.I, Yp.R, Yp.cores))
+        xs.append(X if prec == "fp64" else as32(gpu, X))
+        del Y, Yp, X
+    torch.cuda.synchronize()
+    outs = gpu.tt_round_batched(xs, [1e-6] * len(xs), precision=prec)
+    gots = [down(o) for o in outs]
+    del xs, outs
+    release(gpu)
+    pending = []
+    for t, got in zip(members, gots):
+        ref = pool.get("batched_%d" % t)
+        assert got.R == ref.R, (t, got.R, ref.R)
+        pending.append((t, pool.rel_err_async(got, ref)))
+    errs = {t: p.get(1500) for t, p in pending}
+    bad = {t: e for t, e in errs.items() if not e <= tol}
+    assert not bad, bad

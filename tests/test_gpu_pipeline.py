@@ -66,8 +66,11 @@ def test_pipeline_reduced_size_vs_oracle(gpu, orc, prec, tol):
         got = down(dY)
         assert got.R == Y.R
         assert orc.rel_err(got, Y) <= tol
-        assert abs(gpu.tt_dot(dY, dZ) - dot_ref) <= tol * 10 * abs(dot_ref)
-        assert abs(gpu.tt_norm(dY) - nrm_ref) <= tol * 10 * nrm_ref
+        # FP64: the scalars to the plain-FP64 bar itself; the FP32-storage forms carry
+        # the FP32 rounding of the stored cores into them, so they get a factor 10
+        stol = tol if prec == "fp64" else tol * 10
+        assert abs(gpu.tt_dot(dY, dZ) - dot_ref) <= stol * abs(dot_ref)
+        assert abs(gpu.tt_norm(dY) - nrm_ref) <= stol * nrm_ref
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32x2", 1e-6), ("fp32", 1e-3)])

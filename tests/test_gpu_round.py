@@ -138,3 +138,18 @@ def test_deterministic(gpu, orc):
     assert a.R == b.R
     for ca, cb in zip(a.cores, b.cores):
         assert (ca == cb).all()
+
+
+@pytest.mark.parametrize("core,value", [(0, np.nan), (1, np.nan), (2, np.inf), (3, -np.inf)])
+def test_nonfinite_input_returns_numerical_status(gpu, orc, core, value):
+    # A non-finite entry written on the host into one input core: the rounding runs to
+    # the end (no kernel waits on a value) and reports TT_ERR_NUMERICAL.
+    x = ttgen.random_tt([20, 30, 25, 10], [1, 4, 6, 5, 1], 97)
+    x.cores[core] = x.cores[core].copy()
+    x.cores[core][7] = value
+    with pytest.raises(gpu.TTError) as e:
+        gpu.tt_round(up(gpu, x), 1e-6)
+    assert e.value.status == 4
+    # the library stays usable afterwards
+    ok = ttgen.random_tt([20, 30, 25, 10], [1, 4, 6, 5, 1], 98)
+    check_round(gpu, orc, ok, 1e-6)

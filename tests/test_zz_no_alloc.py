@@ -5,8 +5,8 @@ cudaMalloc's device-wide synchronization is not acceptable in their loop, or the
 where allocating is forbidden.  tt_dot_noalloc serves them with scratch from a fixed
 device array instead of a caller workspace.  This file checks, through the C ABI, that
 it returns what tt_dot returns (within the 1e-12 relative tolerance of the other
-inner-product tests) on two calls in a row, and that it refuses sizes beyond its fixed
-scratch.  It is collected last and passes both alone and after the other tests.
+inner-product tests) on two calls in a row, without changing the device's free memory,
+and that it refuses sizes beyond its fixed scratch.  It is collected last and passes both alone and after the other tests.
 """
 import ctypes
 
@@ -61,10 +61,14 @@ def test_noalloc_matches_tt_dot_twice(lib):
     assert lib.tt_dot(ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(ref), ctypes.c_void_p(ws.data_ptr()),
                       ctypes.c_size_t(ws.numel()), stream) == 0
     scale = np.sqrt(ttgb.tt_dot(da, da) * ttgb.tt_dot(db, db))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     for _ in range(2):
         got = ctypes.c_double(0)
         assert lib.tt_dot_noalloc(ctypes.byref(sa), ctypes.byref(sb), ctypes.byref(got), stream) == 0
         assert abs(got.value - ref.value) <= 1e-12 * scale
+        # nothing was allocated on the device: its free memory is what it was before
+        assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
