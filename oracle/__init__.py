@@ -13,6 +13,8 @@ Algorithms for Tensor Train Arithmetic" (arXiv 2011.06532), cited in oracle.c:
   tt_round    Alg. 2, TT rounding (right-to-left orthonormalization, then
               left-to-right delta-truncation, delta = eps ||X|| / sqrt(N-1))
   tt_orth_right  Alg. 1
+  tt_orth_left   the mirror of Alg. 1 (left-orthonormalization, Sec. 3.4)
+  tt_round_lrl   TT rounding in the LRL ordering (Sec. 3.4, Sec. 4.3.2)
   tt_norm     Sec. 3.2.4, norm through orthonormalization
   tt_dot      Sec. 3.2.3, Eq. innerprodsum (and its two-multiplication form)
   tt_add      Sec. 3.2.1;  tt_hadamard  Sec. 3.2.2
@@ -57,8 +59,11 @@ def _bind(lib):
         "orc_qr": [ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, _f64p],
         "orc_svd": [ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, _f64p, _f64p],
         "orc_tt_orth_right": [ctypes.c_int64, _i64p, _i64p, _f64p, _i64p, _f64p],
+        "orc_tt_orth_left": [ctypes.c_int64, _i64p, _i64p, _f64p, _i64p, _f64p],
         "orc_tt_norm": [ctypes.c_int64, _i64p, _i64p, _f64p, _f64p],
         "orc_tt_round": [ctypes.c_int64, _i64p, _i64p, _f64p, ctypes.c_double, _i64p, _f64p, _f64p, _f64p, _f64p],
+        "orc_tt_round_lrl": [ctypes.c_int64, _i64p, _i64p, _f64p, ctypes.c_double, _i64p, _f64p, _f64p, _f64p,
+                             _f64p],
         "orc_tt_add": [ctypes.c_int64, _i64p, _i64p, _f64p, _i64p, _f64p, _i64p, _f64p],
         "orc_tt_hadamard": [ctypes.c_int64, _i64p, _i64p, _f64p, _i64p, _f64p, _i64p, _f64p],
         "orc_tt_dot": [ctypes.c_int64, _i64p, _i64p, _f64p, _i64p, _f64p, _f64p],
@@ -162,6 +167,32 @@ def tt_round(x: TT, eps: float, lib=None) -> Tuple[TT, RoundInfo]:
     _chk(lib.orc_tt_round(x.N, _pi(I), _pi(R), _p64(flat), float(eps), _pi(Ro), _p64(out), _p64(nrm), _p64(delta),
                           _p64(tails)), "orc_tt_round")
     return from_flat(x.I, Ro, out), RoundInfo(float(nrm[0]), float(delta[0]), tails[: max(x.N - 1, 0)])
+
+
+def tt_round_lrl(x: TT, eps: float, lib=None) -> Tuple[TT, RoundInfo]:
+    """TT rounding in the LRL ordering (Sec. 3.4, Sec. 4.3.2): left-orthonormalization,
+    then truncation from right to left.  tails[n-1] is the cut between cores n-1 and n."""
+    lib = lib or load()
+    I, R, flat = _tt_args(x)
+    Ro = np.zeros(x.N + 1, dtype=np.int64)
+    out = np.zeros_like(flat)
+    nrm = np.zeros(1)
+    delta = np.zeros(1)
+    tails = np.zeros(max(x.N - 1, 1))
+    _chk(lib.orc_tt_round_lrl(x.N, _pi(I), _pi(R), _p64(flat), float(eps), _pi(Ro), _p64(out), _p64(nrm),
+                              _p64(delta), _p64(tails)), "orc_tt_round_lrl")
+    return from_flat(x.I, Ro, out), RoundInfo(float(nrm[0]), float(delta[0]), tails[: max(x.N - 1, 0)])
+
+
+def tt_orth_left(x: TT, lib=None) -> TT:
+    """Left-orthonormalization (the mirror of Alg. 1): V(Y_n) has orthonormal columns
+    for n < N-1 and the tensor is unchanged."""
+    lib = lib or load()
+    I, R, flat = _tt_args(x)
+    Ro = np.zeros(x.N + 1, dtype=np.int64)
+    out = np.zeros_like(flat)
+    _chk(lib.orc_tt_orth_left(x.N, _pi(I), _pi(R), _p64(flat), _pi(Ro), _p64(out)), "orc_tt_orth_left")
+    return from_flat(x.I, Ro, out)
 
 
 def tt_orth_right(x: TT, lib=None) -> TT:

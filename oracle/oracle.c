@@ -387,6 +387,63 @@ int orc_tt_norm(i64 N, const i64 *I, const i64 *R, const double *cores, double *
 }
 
 /* ------------------------------------------------------------------------ */
+/* Left-orthonormalization: the mirror of Alg. 1 ("the approach for left     */
+/* orthonormalization is analogous", Sec. 3.4; left-orthonormal TTs, Sec. 2.3)*/
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For n = 0 up to N-2: QR of V(X_n) = Q R (economy, k = min(R_n I_n, R_{n+1}));
+ * V(X_n) <- Q (rank R_{n+1} becomes k); H(X_{n+1}) <- R H(X_{n+1}), the pass of
+ * the triangular factor to the right neighbour (Eq. nonunique of Sec. 2.1: the
+ * tensor is unchanged).  Afterwards V(X_n) has orthonormal columns for n < N-1
+ * and ||X|| = ||X_N||_F (Sec. 2.3, Sec. 3.2.4).
+ */
+static int left_orth(wtt *w) {
+  for (i64 n = 0; n + 1 < w->N; ++n) {
+    i64 m = w->r[n] * w->I[n], b = w->r[n + 1];
+    i64 k = m < b ? m : b;
+    double *Q = (double *)malloc(sizeof(double) * (size_t)(m * k));
+    double *R = (double *)malloc(sizeof(double) * (size_t)(k * b));
+    i64 cols = w->I[n + 1] * w->r[n + 2];
+    double *T = (double *)malloc(sizeof(double) * (size_t)(k * cols));
+    if (!Q || !R || !T) {
+      free(Q); free(R); free(T);
+      return ORC_ENOMEM;
+    }
+    int st = orc_qr(m, b, w->c[n], Q, R);
+    if (st) {
+      free(Q); free(R); free(T);
+      return st;
+    }
+    /* V(X_n) <- Q (m x k) */
+    memcpy(w->c[n], Q, sizeof(double) * (size_t)(m * k));
+    /* H(X_{n+1}) (b x cols) <- R H(X_{n+1}) (k x cols) */
+    const double *H = w->c[n + 1];
+    for (i64 col = 0; col < cols; ++col)
+      for (i64 a2 = 0; a2 < k; ++a2) {
+        double s = 0.0;
+        for (i64 a = 0; a < b; ++a) s += R[a2 + k * a] * H[a + b * col];
+        T[a2 + k * col] = s;
+      }
+    memcpy(w->c[n + 1], T, sizeof(double) * (size_t)(k * cols));
+    w->r[n + 1] = k;
+    free(Q); free(R); free(T);
+  }
+  return ORC_OK;
+}
+
+int orc_tt_orth_left(i64 N, const i64 *I, const i64 *R, const double *cores, i64 *R_out, double *out) {
+  int st = check_tt(N, I, R);
+  if (st) return st;
+  wtt w;
+  if ((st = wtt_load(&w, N, I, R, cores))) return st;
+  st = left_orth(&w);
+  if (!st) wtt_store(&w, R_out, out);
+  wtt_free(&w);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Alg. 2: TT rounding                                                        */
 /* ------------------------------------------------------------------------ */
 
@@ -490,6 +547,98 @@ int orc_tt_round(i64 N, const i64 *I, const i64 *R, const double *cores, double 
       }
     }
     free(Q); free(Rf); free(Ur); free(S); free(Vr);
+  }
+  if (!st) wtt_store(&w, R_out, out);
+  wtt_free(&w);
+  return st;
+}
+
+/*
+ * TT rounding in the other ordering (Sec. 3.4: "the other ordering works
+ * analogously"; the LRL variant of Sec. 4.3.2): left-orthonormalization, then
+ * truncation from right to left.  ||X|| = ||X_N||_F after the first sweep
+ * (Sec. 2.3), delta = eps ||X|| / sqrt(N-1) as in Alg. 2.  For n = N-1 down to
+ * 1 the SVD of H(X_n) is taken through the QR of its transpose:
+ * H(X_n)^T = Q R, R = Ur S Vr^T, so H(X_n) = Vr S (Q Ur)^T; the rank L follows
+ * the same rule as Alg. 2 (pick_rank), H(X_n) <- (Q Ur(:, :L))^T and
+ * V(X_{n-1}) <- V(X_{n-1}) Vr(:, :L) diag(S(:L)).  Arguments as orc_tt_round;
+ * tails_out[n-1] is the tail discarded at the cut between cores n-1 and n.
+ */
+int orc_tt_round_lrl(i64 N, const i64 *I, const i64 *R, const double *cores, double eps, i64 *R_out, double *out,
+                     double *nrm_out, double *delta_out, double *tails_out) {
+  int st = check_tt(N, I, R);
+  if (st) return st;
+  if (!(eps >= 0.0)) return ORC_EINVAL;
+  wtt w;
+  if ((st = wtt_load(&w, N, I, R, cores))) return st;
+  if (N == 1) {
+    if (nrm_out) *nrm_out = norm2_pairwise(w.c[0], I[0], 1);
+    if (delta_out) *delta_out = 0.0;
+    wtt_store(&w, R_out, out);
+    wtt_free(&w);
+    return ORC_OK;
+  }
+  if ((st = left_orth(&w))) {
+    wtt_free(&w);
+    return st;
+  }
+  double nrm = norm2_pairwise(w.c[N - 1], core_size(w.I, w.r, N - 1), 1);
+  double delta = eps * nrm / sqrt((double)(N - 1));
+  if (nrm_out) *nrm_out = nrm;
+  if (delta_out) *delta_out = delta;
+  for (i64 n = N - 1; n >= 1 && !st; --n) {
+    i64 b = w.r[n], m = w.I[n] * w.r[n + 1];
+    i64 k = m < b ? m : b;
+    double *A = (double *)malloc(sizeof(double) * (size_t)(m * b));
+    double *Q = (double *)malloc(sizeof(double) * (size_t)(m * k));
+    double *Rf = (double *)malloc(sizeof(double) * (size_t)(k * b));
+    double *Ur = (double *)malloc(sizeof(double) * (size_t)(k * k));
+    double *S = (double *)malloc(sizeof(double) * (size_t)k);
+    double *Vr = (double *)malloc(sizeof(double) * (size_t)(b * k));
+    if (!A || !Q || !Rf || !Ur || !S || !Vr) st = ORC_ENOMEM;
+    if (!st) {
+      /* A = H(X_n)^T (m x b) */
+      const double *X = w.c[n];
+      for (i64 a = 0; a < b; ++a)
+        for (i64 col = 0; col < m; ++col) A[col + m * a] = X[a + b * col];
+      st = orc_qr(m, b, A, Q, Rf);
+    }
+    if (!st) st = orc_svd(k, b, Rf, Ur, S, Vr);
+    i64 L = 0;
+    double tail = 0.0;
+    if (!st) {
+      L = pick_rank(k, S, delta, &tail);
+      if (L < 1) st = ORC_ENOMEM;
+    }
+    if (!st) {
+      if (tails_out) tails_out[n - 1] = tail;
+      /* H(X_n) <- (Q Ur(:, :L))^T  (L x m) */
+      double *Xn = w.c[n];
+      for (i64 col = 0; col < m; ++col)
+        for (i64 l = 0; l < L; ++l) {
+          double s = 0.0;
+          for (i64 j = 0; j < k; ++j) s += Q[col + m * j] * Ur[j + k * l];
+          Xn[l + L * col] = s;
+        }
+      /* V(X_{n-1}) (M x b) <- V(X_{n-1}) Vr(:, :L) diag(S(:L))  (M x L) */
+      i64 M = w.r[n - 1] * w.I[n - 1];
+      double *P = w.c[n - 1];
+      double *T = (double *)malloc(sizeof(double) * (size_t)(M * L));
+      if (!T) {
+        st = ORC_ENOMEM;
+      } else {
+        for (i64 l = 0; l < L; ++l)
+          for (i64 row = 0; row < M; ++row) {
+            double s2 = 0.0;
+            for (i64 a = 0; a < b; ++a) s2 += P[row + M * a] * Vr[a + b * l];
+            T[row + M * l] = S[l] * s2;
+          }
+        memcpy(P, T, sizeof(double) * (size_t)(M * L));
+        free(T);
+        w.r[n] = L;
+      }
+    }
+    free(A); free(Q); free(Rf); free(Ur); free(S); free(Vr);
   }
   if (!st) wtt_store(&w, R_out, out);
   wtt_free(&w);

@@ -25,8 +25,8 @@ MUTANTS = {
     "push_dropped": ("    memcpy(P, T, sizeof(double) * (size_t)(M * k));\n    w->r[n] = k;",
                      "    (void)T;\n    w->r[n] = k;"),
     "push_transposed": ("s += P[row + M * a] * R[a2 + k * a];", "s += P[row + M * a] * R[a + k * a2];"),
-    "delta_without_sqrt": ("double delta = eps * nrm / sqrt((double)(N - 1));\n  if (nrm_out)",
-                           "double delta = eps * nrm;\n  if (nrm_out)"),
+    "delta_without_sqrt": ("core_size(w.I, w.r, 0), 1);\n  double delta = eps * nrm / sqrt((double)(N - 1));",
+                           "core_size(w.I, w.r, 0), 1);\n  double delta = eps * nrm;"),
     "rank_rule_strict": ("if (t[l] <= d2) {", "if (t[l] < d2) {"),
     "rank_off_by_one": ("      L = l;\n      break;", "      L = l < k ? l + 1 : l;\n      break;"),
     "house_tau_sign": ("tau[j] = (beta - alpha) / beta;", "tau[j] = (alpha - beta) / beta;"),
@@ -38,6 +38,12 @@ MUTANTS = {
                             "Z[(q * ra0 + p) + r0 * (i + In * (s * rb1 + t))]"),
     "add_block_misplaced": ("i64 row_shift = (n == 0) ? 0 : ra0;", "i64 row_shift = 0;"),
     "dot_sum_dropped": ("Wn[q + qy * s] += acc;", "Wn[q + qy * s] = acc;"),
+    "left_push_transposed": ("s += R[a2 + k * a] * H[a + b * col];", "s += R[a + k * a2] * H[a + b * col];"),
+    "lrl_norm_of_first_core": ("double nrm = norm2_pairwise(w.c[N - 1], core_size(w.I, w.r, N - 1), 1);",
+                               "double nrm = norm2_pairwise(w.c[0], core_size(w.I, w.r, 0), 1);"),
+    "lrl_sigma_not_pushed": ("T[row + M * l] = S[l] * s2;", "T[row + M * l] = s2;"),
+    "lrl_u_transposed": ("for (i64 j = 0; j < k; ++j) s += Q[col + m * j] * Ur[j + k * l];\n          Xn[l + L * col]",
+                         "for (i64 j = 0; j < k; ++j) s += Q[col + m * j] * Ur[l + k * j];\n          Xn[l + L * col]"),
 }
 
 
@@ -134,6 +140,27 @@ def battery(lib):
         ok = ok and np.linalg.norm(full(yt) - f) <= eps * np.linalg.norm(f) * (1 + 1e-9)
         if not ok:
             failed.append(f"round{seed}")
+
+    # left-orthonormalization and the LRL ordering: the TT-SVD of the mode-reversed tensor
+    xl = ttgen.random_tt([4, 3, 5, 3], [1, 3, 4, 2, 1], 9)
+    fl = full(xl)
+    yl = oracle.tt_orth_left(xl, lib=lib)
+    if np.abs(full(yl) - fl).max() > 1e-12 * np.linalg.norm(fl):
+        failed.append("orth_left")
+    for seed, eps in [(1, 1e-3), (2, 1e-1)]:
+        xt = decaying_tt([3, 4, 5, 4, 3], 6, 90 + seed)
+        f = full(xt)
+        try:
+            yt, _ = oracle.tt_round_lrl(xt, eps, lib=lib)
+        except oracle.OracleError:
+            failed.append(f"lrl{seed}")
+            continue
+        g = np.transpose(f, axes=tuple(range(f.ndim - 1, -1, -1)))
+        ranks, fref = numpy_tt_svd_ranks_and_full(g, eps)
+        fref = np.transpose(fref, axes=tuple(range(f.ndim - 1, -1, -1)))
+        ok = yt.R == ranks[::-1] and np.abs(full(yt) - fref).max() < 1e-11 * np.linalg.norm(f)
+        if not ok:
+            failed.append(f"lrl{seed}")
 
     z = TT([3, 4, 2], [1, 2, 3, 1], [np.zeros(6), np.zeros(24), np.zeros(6)])
     try:

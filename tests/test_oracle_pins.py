@@ -210,6 +210,21 @@ def test_right_orth_invariants(orc):
     assert abs(orc.tt_norm(x) - np.linalg.norm(f)) < 1e-13 * np.linalg.norm(f)
 
 
+def test_left_orth_invariants(orc):
+    # the mirror of Alg. 1 (Sec. 3.4): V(Y_n) has orthonormal columns for n < N-1 (Sec. 2.3),
+    # the tensor is unchanged (Eq. nonunique) and ||X|| = ||Y_N||_F (Sec. 2.3, Sec. 3.2.4)
+    I = [4, 6, 5, 3, 4]
+    x = ttgen.random_tt(I, [1, 3, 5, 4, 2, 1], 53)
+    y = orc.tt_orth_left(x)
+    assert left_orth_err(y) < 1e-13
+    f = full_by_entries(x)
+    np.testing.assert_allclose(full_by_entries(y), f, rtol=1e-12, atol=1e-14)
+    assert abs(np.linalg.norm(y.cores[-1]) - np.linalg.norm(f)) < 1e-13 * np.linalg.norm(f)
+    # wide unfoldings: the first cut is capped by R_0 I_0 = 2
+    z = orc.tt_orth_left(ttgen.random_tt([2, 3, 3, 2], [1, 5, 7, 5, 1], 54))
+    assert z.R == [1, 2, 6, 5, 1]
+
+
 def test_norm_ortho_accurate_for_small_norm(orc):
     # Sec. 3.2.4: the orthonormalization norm avoids the cancellation of <X,X>.
     x = ttgen.random_tt([8, 9, 7, 6], [1, 4, 5, 3, 1], 52)
@@ -231,6 +246,14 @@ def decaying_tt(I, r, seed, rate=0.5):
         c = x.core3(n) * (rate ** np.arange(r))[None, None, :]
         x.cores[n] = np.asfortranarray(c).ravel(order="F")
     return x
+
+
+def right_orth_err(y: TT):
+    e = 0.0
+    for n in range(1, y.N):
+        H = y.cores[n].reshape((y.R[n], -1), order="F")
+        e = max(e, np.abs(H @ H.T - np.eye(y.R[n])).max())
+    return e
 
 
 def left_orth_err(y: TT):
@@ -268,6 +291,74 @@ def test_round_matches_tt_svd_bruteforce(orc, seed, eps):
     if tails > 1e-20 * np.linalg.norm(f) ** 2:
         assert abs(err ** 2 - tails) <= 1e-8 * tails + 1e-26
     assert left_orth_err(y) < 1e-13
+
+
+def reversed_tt_svd(f, eps):
+    """Right-to-left TT-SVD of the full tensor f, through numpy's LAPACK SVD: the
+    textbook left-to-right TT-SVD (sequential truncated SVDs of the unfoldings, same
+    delta rule) of f with its modes in reverse order, then the modes put back."""
+    g = np.transpose(f, axes=tuple(range(f.ndim - 1, -1, -1)))
+    N = g.ndim
+    delta = eps * np.linalg.norm(g) / np.sqrt(N - 1)
+    C = g.reshape(g.shape[0], -1, order="F")
+    ranks, r, Us = [1], 1, []
+    for n in range(N - 1):
+        C = C.reshape(r * g.shape[n], -1, order="F")
+        U, S, Vt = np.linalg.svd(C, full_matrices=False)
+        tail = np.concatenate([np.cumsum((S ** 2)[::-1])[::-1], [0.0]])
+        L = next(l for l in range(1, len(S) + 1) if tail[l] <= delta ** 2)
+        Us.append(U[:, :L])
+        C = S[:L, None] * Vt[:L]
+        r = L
+        ranks.append(L)
+    ranks.append(1)
+    T = Us[0]
+    for U in Us[1:]:
+        T = (T @ U.reshape(T.shape[1], -1, order="F")).reshape(-1, U.shape[1], order="F")
+    T = (T @ C).reshape(g.shape, order="F")
+    return ranks[::-1], np.transpose(T, axes=tuple(range(N - 1, -1, -1)))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("eps", [1e-1, 1e-3, 1e-8])
+def test_round_lrl_matches_reversed_tt_svd_bruteforce(orc, seed, eps):
+    # LRL ordering (Sec. 3.4, Sec. 4.3.2): left-orthonormalization, then truncation from
+    # the right; in exact arithmetic the TT-SVD of the mode-reversed tensor
+    I = [3, 4, 5, 4, 3] if seed != 2 else [6, 5, 6, 4]
+    x = decaying_tt(I, 6, 60 + seed)
+    f = full_by_entries(x)
+    y, info = orc.tt_round_lrl(x, eps)
+    ranks, fref = reversed_tt_svd(f, eps)
+    assert y.R == ranks
+    fy = full_by_entries(y)
+    np.testing.assert_allclose(fy, fref, rtol=0, atol=1e-12 * np.linalg.norm(f))
+    err = np.linalg.norm(fy - f)
+    assert err <= eps * np.linalg.norm(f) * (1 + 1e-12) + 1e-14  # Ensure clause of Alg. 2
+    tails = float(np.sum(info.tails))
+    if tails > 1e-20 * np.linalg.norm(f) ** 2:
+        assert abs(err ** 2 - tails) <= 1e-8 * tails + 1e-26
+    assert right_orth_err(y) < 1e-13  # truncation from the right leaves H(Y_n) row-orthonormal
+    assert abs(info.nrm - np.linalg.norm(f)) < 1e-13 * np.linalg.norm(f)
+
+
+def test_round_lrl_x_plus_x_and_n2(orc):
+    x = ttgen.random_tt([5, 4, 6, 3], [1, 3, 4, 2, 1], 72)
+    y, _ = orc.tt_round_lrl(orc.tt_add(x, x), 1e-10)
+    assert y.R == x.R
+    np.testing.assert_allclose(full_by_entries(y), 2 * full_by_entries(x), atol=1e-13)
+    # N = 2: the Eckart-Young truncation of the matrix, whichever the ordering
+    rng = np.random.default_rng(8)
+    U0, V0 = rand_orth(rng, 20, 8), rand_orth(rng, 15, 8)
+    s = 2.0 ** -np.arange(8)
+    A = (U0 * s) @ V0.T
+    xm = TT([20, 15], [1, 8, 1], [U0.ravel(order="F"), (s[:, None] * V0.T).ravel(order="F")])
+    ym, _ = orc.tt_round_lrl(xm, 0.05)
+    Ua, Sa, Vta = np.linalg.svd(A)
+    delta = 0.05 * np.linalg.norm(A)
+    tail = np.cumsum((Sa ** 2)[::-1])[::-1]
+    L = next(l for l in range(1, len(Sa) + 1) if (tail[l] if l < len(Sa) else 0.0) <= delta ** 2)
+    assert ym.R[1] == L
+    np.testing.assert_allclose(full_by_entries(ym), (Ua[:, :L] * Sa[:L]) @ Vta[:L], atol=1e-13)
 
 
 def test_round_n2_is_eckart_young(orc):
