@@ -46,7 +46,8 @@ def parse_args():
     p.add_argument("--modes", type=int, default=I_MODE, help="mode size I_n (default: the full 65536)")
     p.add_argument("--variants", type=int, default=1,
                    help="1: also time the mixed-precision and batched forms (N=1 only), 0: skip")
-    p.add_argument("--batch", type=int, default=64, help="tensors of the batched recipe timed in the variants")
+    p.add_argument("--batch", type=int, default=512, help="tensors of the batched recipe timed in the variants")
+    p.add_argument("--chunk", type=int, default=64, help="batched-recipe tensors resident at once")
     return p.parse_args()
 
 
@@ -264,7 +265,7 @@ def run_variants(args):
     """Decaying-spectrum workload (N=50, I_n=16384, formal ranks 64, eps=1e-5) in fp64,
     fp32x2 and fp32, and the first `args.batch` tensors of the 512-tensor batched recipe
     (N in 4..20, I_n in 64..4096, ranks 2r with r in 4..48, eps=1e-6): a loop of FP64
-    roundings against one graph-captured batch in fp32x2 and fp32."""
+    roundings against graph-captured batches in FP64, fp32x2 and fp32."""
     import torch
 
     import paper_2011_06532_gb300 as ttgb
@@ -305,21 +306,35 @@ def run_variants(args):
     ttgb._ws_cache.clear()
     torch.cuda.empty_cache()
 
-    # ---- batched recipe: FP64 loop vs one graph-captured batch
+    # ---- batched recipe: the whole 512-tensor recipe in chunks (its FP64 form, 290 GB, does
+    # not fit in HBM at once): per chunk a loop of FP64 roundings, one graph-captured FP64
+    # batch, and graph-captured batches in fp32x2 and fp32; times summed over the chunks
+    out["batched_%d" % args.batch] = run_batched_recipe(args)
+    torch.cuda.empty_cache()
+    out["hadamard_pipeline"] = run_pipeline(args)
+    out["paper_model1"] = run_model1(args)
+    return out
+
+
+def run_batched_recipe(args):
+    """The first args.batch tensors of the batched recipe, args.chunk at a time (inputs drawn on
+    the device with the recipe's shapes; timing only).  Per chunk: a Python loop of FP64
+    tt_round calls (each synchronizes the host), one graph-captured FP64 batch (isolates the
+    gain from concurrency), then graph-captured fp32x2 and fp32 batches (the precision gain
+    on top).  Ranks of every batched form are compared with the FP64 loop's."""
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+    import ttgen
+
     shapes = ttgen.batched_shapes()[: args.batch]
-    X64 = []
-    for t, (I, r) in enumerate(shapes):
-        (I_, R, Y), (_, _, Yp) = ttgen.device_perturbed_pair(I, r, ttgen.BASE_SEED + 4 + 97 * t)
-        X64.append(ttgb.tt_add(ttgb.DeviceTT(I_, R, Y), ttgb.DeviceTT(I_, R, Yp)))
-    torch.cuda.synchronize()
-    X32 = [ttgb.DeviceTT(x.I, x.R, [c.float() for c in x.cores]) for x in X64]
-    eps = [1e-6] * len(X64)
-    res = {"tensors": len(X64), "input_gb_fp32": sum(x.nbytes() for x in X32) / 1e9}
-    t_loop = _time(lambda: [ttgb.tt_round(x, 1e-6) for x in X64], reps=1)
-    res["fp64_loop"] = {"tts_per_s": len(X64) / t_loop, "ms": t_loop * 1e3}
-    ref = [ttgb.tt_round(x, 1e-6) for x in X64]
-    for prec in ("fp32x2", "fp32"):
-        b = ttgb.Batch(X32, eps, prec)
+    tot = {"fp64_loop": 0.0, "fp64_graph": 0.0, "fp32x2_graph": 0.0, "fp32_graph": 0.0}
+    tuned = None
+    equal = {k: True for k in tot if k != "fp64_loop"}
+    gb32 = 0.0
+
+    def graph_time(xs, prec):
+        b = ttgb.Batch(xs, [1e-6] * len(xs), prec)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -329,39 +344,62 @@ def run_variants(args):
         with torch.cuda.graph(g, stream=s):
             b.enqueue(s)
         t = _time(g.replay, reps=1)
-        got = b.outputs()
-        res[prec + "_graph"] = {"tts_per_s": len(X64) / t, "ms": t * 1e3, "speedup_vs_fp64_loop": t_loop / t,
-                                "ranks_equal": all(a.R == o.R for a, o in zip(ref, got))}
-        if prec != "fp32x2":
-            del b, g
-            torch.cuda.empty_cache()
-            continue
-        # the same batch after tuning its leaf/tile policy on the GPU
-        t0 = time.perf_counter()
-        b.autotune()
-        tune_s = time.perf_counter() - t0
-        with torch.cuda.stream(s):
-            b.enqueue(s)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=s):
-            b.enqueue(s)
-        t = _time(g.replay, reps=1)
-        got = b.outputs()
-        caps = sorted({int(ln.split()[7]) for ln in ttgb.tune_export().splitlines()
-                       if ln and not ln.startswith("#") and int(ln.split()[7]) < int(ln.split()[2])})
-        res[prec + "_graph_tuned"] = {"tts_per_s": len(X64) / t, "ms": t * 1e3, "speedup_vs_fp64_loop": t_loop / t,
-                                      "ranks_equal": all(a.R == o.R for a, o in zip(ref, got)), "tuning_s": tune_s,
-                                      "leaf_cap": caps[0] if caps else None}
+        outs = b.outputs()
         del b, g
+        return t, outs
+
+    for c0 in range(0, len(shapes), args.chunk):
+        X64 = []
+        for t, (I, r) in enumerate(shapes[c0:c0 + args.chunk]):
+            (I_, R, Y), (_, _, Yp) = ttgen.device_perturbed_pair(I, r, ttgen.BASE_SEED + 4 + 97 * (c0 + t))
+            X64.append(ttgb.tt_add(ttgb.DeviceTT(I_, R, Y), ttgb.DeviceTT(I_, R, Yp)))
+            del Y, Yp
+        torch.cuda.synchronize()
+        t = _time(lambda: [ttgb.tt_round(x, 1e-6) for x in X64], reps=1)
+        tot["fp64_loop"] += t
+        ref = [ttgb.tt_round(x, 1e-6).R for x in X64]
+        ttgb._ws_cache.clear()
+        t, outs = graph_time(X64, "fp64")
+        tot["fp64_graph"] += t
+        equal["fp64_graph"] &= all(a == o.R for a, o in zip(ref, outs))
+        del outs
+        X32 = [ttgb.DeviceTT(x.I, x.R, [c.float() for c in x.cores]) for x in X64]
+        gb32 += sum(x.nbytes() for x in X32) / 1e9
+        del X64
         torch.cuda.empty_cache()
-    ttgb.tune_clear()
-    out["batched_first%d" % len(X64)] = res
-    del X64, X32, ref
-    torch.cuda.empty_cache()
-    out["hadamard_pipeline"] = run_pipeline(args)
-    out["paper_model1"] = run_model1(args)
-    return out
+        for prec in ("fp32x2", "fp32"):
+            t, outs = graph_time(X32, prec)
+            tot[prec + "_graph"] += t
+            equal[prec + "_graph"] &= all(a == o.R for a, o in zip(ref, outs))
+            del outs
+            torch.cuda.empty_cache()
+            if prec == "fp32x2" and c0 == 0:
+                # the autotuner's batch policy on the first chunk (tt_autotune_batched)
+                b = ttgb.Batch(X32, [1e-6] * len(X32), prec)
+                t0 = time.perf_counter()
+                b.autotune()
+                tune_s = time.perf_counter() - t0
+                del b
+                t2, outs = graph_time(X32, prec)
+                caps = sorted({int(ln.split()[7]) for ln in ttgb.tune_export().splitlines()
+                               if ln and not ln.startswith("#") and int(ln.split()[7]) < int(ln.split()[2])})
+                tuned = {"tensors": len(X32), "ms_default": t * 1e3, "ms_tuned": t2 * 1e3, "tuning_s": tune_s,
+                         "leaf_cap": caps[0] if caps else None,
+                         "ranks_equal": all(a == o.R for a, o in zip(ref, outs))}
+                del outs
+                ttgb.tune_clear()
+                torch.cuda.empty_cache()
+        del X32
+        torch.cuda.empty_cache()
+    n = len(shapes)
+    res = {"tensors": n, "chunk": args.chunk, "input_gb_fp32": gb32, "first_chunk_fp32x2_autotuned": tuned}
+    for k, v in tot.items():
+        res[k] = {"tts_per_s": n / v, "ms": v * 1e3}
+        if k != "fp64_loop":
+            res[k].update({"speedup_vs_fp64_loop": tot["fp64_loop"] / v, "ranks_equal": equal[k]})
+        if k.startswith("fp32"):
+            res[k]["speedup_vs_fp64_graph"] = tot["fp64_graph"] / v
+    return res
 
 
 def run_model1(args):

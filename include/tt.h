@@ -8,6 +8,8 @@
  *   tt_hadamard  Sec. 3.2.2 (Hadamard product)
  *   tt_dot       Sec. 3.2.3, Eq. innerprodsum (inner product)
  *   tt_norm      Sec. 3.2.4 (norm through orthonormalization)
+ *   tt_orthonormalize  Alg. 1 / Alg. 5 and the left-hand mirror (Sec. 3.4)
+ *   tt_round_ordered   the RLR and LRL orderings of rounding (Sec. 3.4, 4.3.2)
  *
  * Tensor layout.  A TT tensor X has N >= 1 cores; core n (0-based) is an
  * R[n] x I[n] x R[n+1] array with R[0] = R[N] = 1 (Sec. 2.1).  Entry (a, i, b)
@@ -122,6 +124,78 @@ int tt_round_workspace_size(const tt_tensor *x, int precision, size_t *bytes);
  */
 int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void *workspace, size_t workspace_bytes,
              void *stream);
+
+/*
+ * Orderings of TT rounding (Sec. 3.4; the RLR and LRL variants of Sec. 4.3.2).
+ * TT_ORDER_RLR: right-to-left orthonormalization, then truncation from the left
+ * (Alg. 2, Alg. 6; what tt_round computes).  TT_ORDER_LRL: left-to-right
+ * orthonormalization (QR of every V(X_n), n = 1..N-1, R pushed into core n+1),
+ * ||X|| = ||X_N||_F, then truncation from the right: for n = N..2 the SVD of
+ * H(X_n) (through the QR of H(X_n)^T), the same rank rule with delta =
+ * eps ||X|| / sqrt(N-1), H(Y_n) <- the leading L_{n-1} right singular vectors
+ * (rows orthonormal) and V(X_{n-1}) <- V(X_{n-1}) V_hat Sigma_hat.  Both satisfy
+ * ||X - Y|| <= eps ||X||; their results differ by O(delta).
+ */
+typedef enum { TT_ORDER_RLR = 0, TT_ORDER_LRL = 1 } tt_order;
+
+/* Workspace bytes of tt_round_ordered (TT_ORDER_LRL: about twice the input size
+ * more than tt_round, for the mode-reversed copies described below). */
+int tt_round_ordered_workspace_size(const tt_tensor *x, int precision, int order, size_t *bytes);
+
+/*
+ * tt_round in the given ordering; arguments, results and errors as tt_round
+ * (TT_ORDER_RLR is tt_round itself).  TT_ORDER_LRL runs the right-to-left
+ * kernels on the mode-reversed tensor (core m = X_{N-1-m} with its rank indices
+ * swapped, whose transposed horizontal unfoldings are the vertical unfoldings
+ * of X up to a row permutation, which leaves every R factor unchanged), then
+ * reverses the result: two extra memory-bound passes, one over the input and one
+ * over the output, in the workspace.  Synchronizes `stream`.
+ */
+int tt_round_ordered(const tt_tensor *x, double eps, int precision, int order, tt_tensor *out, void *workspace,
+                     size_t workspace_bytes, void *stream);
+
+/* Workspace bytes of tt_round_hadamard (those of rounding the product's shape). */
+int tt_round_hadamard_workspace_size(const tt_tensor *a, const tt_tensor *b, int precision, size_t *bytes);
+
+/*
+ * Rounding of a Hadamard product (Sec. 3.2.2 followed by Alg. 2 / Alg. 6) without
+ * forming it: Y = round(A o B, eps) with the same result as tt_hadamard followed by
+ * tt_round, but the product's cores (R_A R_B x I x R_A' R_B', Kronecker order as in
+ * tt_hadamard) are never written: the kernels that read input cores (the
+ * orthogonalization sweep and the first core) form each entry A_n(p, i, s) B_n(q, i, t)
+ * where they use it.  In FP32 storage the products are formed exactly (a double-float
+ * pair for TT_PREC_FP32X2), not rounded to FP32 first.  a and b share N, dtype and I;
+ * the product ranks must be supported (as tt_round's); out->cores[n] must hold
+ * R_A[n] R_B[n] I[n] R_A[n+1] R_B[n+1] elements; out->R receives the new ranks.
+ * Workspace and errors as tt_round.  Synchronizes `stream`.
+ */
+int tt_round_hadamard(const tt_tensor *a, const tt_tensor *b, double eps, int precision, tt_tensor *out,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Orthonormalization with explicit factors (Alg. 1, parallel form Alg. 5; the
+ * left-hand side is its mirror, Sec. 3.4).  TT_ORTH_RIGHT: for n = N..2 the QR of
+ * H(X_n)^T = Q R, H(Y_n) <- Q^T (orthonormal rows), R pushed into core n-1; core 1
+ * carries the tensor's scale, ||X|| = ||Y_1||_F.  TT_ORTH_LEFT: for n = 1..N-1 the
+ * QR of V(X_n) = Q R, V(Y_n) <- Q (orthonormal columns), R pushed into core n+1;
+ * ||X|| = ||Y_N||_F.  Ranks become K (right: K_n = min(R_n, I_n K_{n+1}); left:
+ * the mirror), known from the shapes.
+ */
+typedef enum { TT_ORTH_RIGHT = 0, TT_ORTH_LEFT = 1 } tt_orth_side;
+
+/* Workspace bytes of tt_orthonormalize (TT_ORTH_LEFT adds the mode-reversed copies). */
+int tt_orthonormalize_workspace_size(const tt_tensor *x, int precision, int side, size_t *bytes);
+
+/*
+ * x, precision, out and workspace as in tt_round: out->cores[n] must hold
+ * x->R[n] I[n] x->R[n+1] elements; out->R is written (on the host, before any
+ * work runs).  The input tensor's scale is carried by the end core (first core
+ * for TT_ORTH_RIGHT, last for TT_ORTH_LEFT); in FP32 storage a tensor whose norm
+ * is outside the FP32 range over- or underflows there.  Asynchronous: the work is
+ * queued on `stream` and the call returns without synchronizing.
+ */
+int tt_orthonormalize(const tt_tensor *x, int precision, int side, tt_tensor *out, void *workspace,
+                      size_t workspace_bytes, void *stream);
 
 /*
  * Batched rounding of `count` independent tensors (each as in tt_round, eps[k]

@@ -22,11 +22,14 @@ from . import _native
 from ._native import build  # noqa: F401  (re-export)
 
 __all__ = ["DeviceTT", "Batch", "build", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard", "tt_dot", "tt_norm",
-           "TTError", "from_host", "to_host", "trace", "trace_read"]
+           "tt_orthonormalize", "tt_round_hadamard", "TTError", "from_host", "to_host", "trace", "trace_read"]
 
 _DTYPES = {torch.float64: 0, torch.float32: 1}
 # tt_precision: "default" (fp64 for float64 cores, fp32x2 for float32), "fp64", "fp32x2", "fp32"
 PRECISIONS = {"default": 0, "fp64": 1, "fp32x2": 2, "fp32": 3}
+# tt_order: "rlr" (right-to-left orthonormalization, truncation from the left; Alg. 2) or "lrl"
+ORDERS = {"rlr": 0, "lrl": 1}
+SIDES = {"right": 0, "left": 1}
 
 
 class TTError(RuntimeError):
@@ -122,10 +125,12 @@ def round_workspace_size(x: DeviceTT, precision: str = "default") -> int:
 
 
 def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tensor]] = None,
-             workspace: Optional[torch.Tensor] = None, precision: str = "default") -> DeviceTT:
+             workspace: Optional[torch.Tensor] = None, precision: str = "default", order: str = "rlr") -> DeviceTT:
     """TT rounding (Alg. 2 / Alg. 6): returns Y with ||X - Y|| <= eps ||X||.
 
     precision: "default", "fp64" (float64 cores), "fp32x2" or "fp32" (float32 cores).
+    order: "rlr" (right-to-left orthonormalization, then truncation from the left, as in
+    Alg. 2) or "lrl" (the mirror ordering, Sec. 4.3.2).
     Cores (of x and of out) may be CUDA tensors or pinned host tensors; the kernels read
     and write pinned host cores directly over the host link.  Without `out`, the result
     cores are allocated where x's are."""
@@ -135,9 +140,14 @@ def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tens
     lib = _native.load()
     dev = _cuda_device(x)
     prec = PRECISIONS[precision]
+    od = ORDERS[order]
     d = _Desc(x.I, x.R, x.cores, x.dtype)
     n = ctypes.c_size_t(0)
-    _check(lib.tt_round_workspace_size(d.ref, prec, ctypes.byref(n)), "tt_round_workspace_size")
+    if od == 0:
+        _check(lib.tt_round_workspace_size(d.ref, prec, ctypes.byref(n)), "tt_round_workspace_size")
+    else:
+        _check(lib.tt_round_ordered_workspace_size(d.ref, prec, od, ctypes.byref(n)),
+               "tt_round_ordered_workspace_size")
     ws = workspace if workspace is not None else _workspace(int(n.value), dev)
     if out is None:
         if x.cores[0].is_cuda:
@@ -145,11 +155,36 @@ def tt_round(x: DeviceTT, eps: float, stream=None, out: Optional[List[torch.Tens
         else:
             out = [torch.empty(s, dtype=x.dtype, pin_memory=True) for s in x.core_sizes()]
     o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
-    _check(lib.tt_round(d.ref, float(eps), prec, o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
-                        _stream(stream)), "tt_round")
+    if od == 0:
+        _check(lib.tt_round(d.ref, float(eps), prec, o.ref, ctypes.c_void_p(ws.data_ptr()),
+                            ctypes.c_size_t(ws.numel()), _stream(stream)), "tt_round")
+    else:
+        _check(lib.tt_round_ordered(d.ref, float(eps), prec, od, o.ref, ctypes.c_void_p(ws.data_ptr()),
+                                    ctypes.c_size_t(ws.numel()), _stream(stream)), "tt_round_ordered")
     R = o.ranks()
     cores = [out[k][: R[k] * x.I[k] * R[k + 1]] for k in range(x.N)]
     return DeviceTT(list(x.I), R, cores)
+
+
+def tt_orthonormalize(x: DeviceTT, side: str = "right", precision: str = "default", stream=None) -> DeviceTT:
+    """Orthonormalization with explicit factors (Alg. 1 / Alg. 5): side "right" makes
+    H(Y_n) row-orthonormal for n >= 2 (the scale in core 1), "left" makes V(Y_n)
+    column-orthonormal for n <= N-1 (the scale in core N).  Queued on the stream."""
+    _validate(x)
+    lib = _native.load()
+    dev = x.cores[0].device
+    prec = PRECISIONS[precision]
+    sd = SIDES[side]
+    d = _Desc(x.I, x.R, x.cores, x.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_orthonormalize_workspace_size(d.ref, prec, sd, ctypes.byref(n)), "tt_orthonormalize_workspace_size")
+    ws = _workspace(int(n.value), dev)
+    out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
+    o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
+    _check(lib.tt_orthonormalize(d.ref, prec, sd, o.ref, ctypes.c_void_p(ws.data_ptr()), ctypes.c_size_t(ws.numel()),
+                                 _stream(stream)), "tt_orthonormalize")
+    R = o.ranks()
+    return DeviceTT(list(x.I), R, [out[k][: R[k] * x.I[k] * R[k + 1]] for k in range(x.N)])
 
 
 def autotune(x: DeviceTT, eps: float, precision: str = "default", stream=None) -> DeviceTT:
@@ -319,6 +354,28 @@ def tt_hadamard(a: DeviceTT, b: DeviceTT, stream=None) -> DeviceTT:
     o = _Desc(a.I, R, out, a.dtype)
     _check(lib.tt_hadamard(da.ref, db.ref, o.ref, _stream(stream)), "tt_hadamard")
     return DeviceTT(list(a.I), o.ranks(), out)
+
+
+def tt_round_hadamard(a: DeviceTT, b: DeviceTT, eps: float, stream=None, precision: str = "default") -> DeviceTT:
+    """round(A o B, eps) without forming the Hadamard product (its entries are formed
+    where the rounding reads them); same result as tt_round(tt_hadamard(a, b), eps)."""
+    _validate(a)
+    _validate(b)
+    lib = _native.load()
+    dev = a.cores[0].device
+    prec = PRECISIONS[precision]
+    da, db = _Desc(a.I, a.R, a.cores, a.dtype), _Desc(b.I, b.R, b.cores, b.dtype)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_round_hadamard_workspace_size(da.ref, db.ref, prec, ctypes.byref(n)),
+           "tt_round_hadamard_workspace_size")
+    ws = _workspace(int(n.value), dev)
+    Rz = [a.R[k] * b.R[k] for k in range(a.N + 1)]
+    out = [torch.empty(Rz[k] * a.I[k] * Rz[k + 1], dtype=a.dtype, device=dev) for k in range(a.N)]
+    o = _Desc(a.I, [1] * (a.N + 1), out, a.dtype)
+    _check(lib.tt_round_hadamard(da.ref, db.ref, float(eps), prec, o.ref, ctypes.c_void_p(ws.data_ptr()),
+                                 ctypes.c_size_t(ws.numel()), _stream(stream)), "tt_round_hadamard")
+    R = o.ranks()
+    return DeviceTT(list(a.I), R, [out[k][: R[k] * a.I[k] * R[k + 1]] for k in range(a.N)])
 
 
 def tt_dot(a: DeviceTT, b: DeviceTT, stream=None) -> float:

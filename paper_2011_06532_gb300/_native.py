@@ -18,7 +18,7 @@ CSRC = os.path.join(_HERE, "csrc")
 INCLUDE = os.path.join(_ROOT, "include")
 BUILD = os.path.join(_HERE, "_build")
 LIB = os.path.join(BUILD, "libttgb.so")
-SOURCES = ["tt_round.cu", "tt_ops.cu", "tt_api.cu", "tt_tune.cu"]
+SOURCES = ["tt_round.cu", "tt_ops.cu", "tt_api.cu", "tt_tune.cu", "tt_orth.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -78,6 +78,8 @@ EXPORTS = [
     "tt_trace", "tt_trace_read", "tt_dot_noalloc", "tt_round_batched_workspace_size", "tt_round_batched_async",
     "tt_autotune_workspace_size", "tt_autotune", "tt_autotune_batched_workspace_size", "tt_autotune_batched",
     "tt_tune_export", "tt_tune_import", "tt_tune_clear", "tt_tune_generation",
+    "tt_round_ordered_workspace_size", "tt_round_ordered", "tt_orthonormalize_workspace_size", "tt_orthonormalize",
+    "tt_round_hadamard_workspace_size", "tt_round_hadamard",
 ]
 KERNEL_KINDS = ["s1_leaf", "tree_factor", "tree_apply", "s2_leaf", "s2_out", "svd", "add", "hadamard", "dot", "misc"]
 
@@ -116,6 +118,12 @@ def load(path: str | None = None):
         "tt_tune_export": [ctypes.c_char_p, ctypes.c_size_t, sz],
         "tt_tune_import": [ctypes.c_char_p],
         "tt_tune_clear": [],
+        "tt_round_ordered_workspace_size": [T, ctypes.c_int, ctypes.c_int, sz],
+        "tt_round_ordered": [T, ctypes.c_double, ctypes.c_int, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_orthonormalize_workspace_size": [T, ctypes.c_int, ctypes.c_int, sz],
+        "tt_orthonormalize": [T, ctypes.c_int, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_round_hadamard_workspace_size": [T, T, ctypes.c_int, sz],
+        "tt_round_hadamard": [T, T, ctypes.c_double, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

@@ -178,6 +178,110 @@ int tt_round(const tt_tensor *x, double eps, int precision, tt_tensor *out, void
   return ttgb::round_run(x, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
 }
 
+int tt_round_ordered_workspace_size(const tt_tensor *x, int precision, int order, size_t *bytes) {
+  if (order == TT_ORDER_RLR) return tt_round_workspace_size(x, precision, bytes);
+  if (order != TT_ORDER_LRL || !valid_tensor(x) || !bytes) return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (x->N == 1) {
+    *bytes = 0;
+    return TT_OK;
+  }
+  return ttgb::round_lrl_workspace(x, prec, bytes);
+}
+
+int tt_round_ordered(const tt_tensor *x, double eps, int precision, int order, tt_tensor *out, void *workspace,
+                     size_t workspace_bytes, void *stream) {
+  if (order == TT_ORDER_RLR) return tt_round(x, eps, precision, out, workspace, workspace_bytes, stream);
+  if (order != TT_ORDER_LRL) return TT_ERR_INVALID_ARG;
+  if (!valid_tensor(x) || !valid_out(x, out) || !(eps >= 0.0) || !isfinite(eps)) return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (!cores_accessible(x) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
+  if (x->N == 1) return ttgb::round_run(x, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
+  return ttgb::round_lrl_run(x, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
+}
+
+namespace {
+// Shape of the Hadamard product of a and b (ranks multiply), cores unset.
+struct ProductShape {
+  std::vector<int64_t> R;
+  std::vector<void *> cores;
+  tt_tensor t{};
+  ProductShape(const tt_tensor *a, const tt_tensor *b) {
+    R.resize(a->N + 1);
+    cores.assign(a->N, nullptr);
+    for (int n = 0; n <= a->N; ++n) R[n] = a->R[n] * b->R[n];
+    t.N = a->N;
+    t.dtype = a->dtype;
+    t.I = a->I;
+    t.R = R.data();
+    t.cores = cores.data();
+  }
+};
+}  // namespace
+
+int tt_round_hadamard_workspace_size(const tt_tensor *a, const tt_tensor *b, int precision, size_t *bytes) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !bytes) return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(a, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  ProductShape z(a, b);
+  if (!ranks_supported(&z.t)) return TT_ERR_UNSUPPORTED;
+  if (a->N == 1) {
+    *bytes = 0;
+    return TT_OK;
+  }
+  return ttgb::round_workspace(&z.t, prec, bytes);
+}
+
+int tt_round_hadamard(const tt_tensor *a, const tt_tensor *b, double eps, int precision, tt_tensor *out,
+                      void *workspace, size_t workspace_bytes, void *stream) {
+  if (!valid_tensor(a) || !valid_tensor(b) || !same_modes(a, b) || !valid_out(a, out) || !(eps >= 0.0) ||
+      !isfinite(eps))
+    return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(a, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  ProductShape z(a, b);
+  if (!ranks_supported(&z.t)) return TT_ERR_UNSUPPORTED;
+  if (!cores_accessible(a) || !cores_accessible(b) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
+  if (a->N == 1) {
+    // a single core: the rounding is a copy of the entrywise product
+    int st = ttgb::hadamard_run(a, b, out, as_stream(stream));
+    if (st) return st;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return TT_ERR_CUDA;
+    out->R[0] = out->R[1] = 1;
+    return TT_OK;
+  }
+  return ttgb::round_hadamard_run(a, b, &z.t, eps, prec, out, workspace, workspace_bytes, as_stream(stream));
+}
+
+int tt_orthonormalize_workspace_size(const tt_tensor *x, int precision, int side, size_t *bytes) {
+  if (!valid_tensor(x) || !bytes || (side != TT_ORTH_RIGHT && side != TT_ORTH_LEFT)) return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (x->N == 1) {
+    *bytes = 0;
+    return TT_OK;
+  }
+  return side == TT_ORTH_RIGHT ? ttgb::orth_workspace(x, prec, bytes) : ttgb::orth_left_workspace(x, prec, bytes);
+}
+
+int tt_orthonormalize(const tt_tensor *x, int precision, int side, tt_tensor *out, void *workspace,
+                      size_t workspace_bytes, void *stream) {
+  if (!valid_tensor(x) || !valid_out(x, out) || (side != TT_ORTH_RIGHT && side != TT_ORTH_LEFT))
+    return TT_ERR_INVALID_ARG;
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (!cores_accessible(x) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
+  if (x->N == 1 || side == TT_ORTH_RIGHT)
+    return ttgb::orth_enqueue(x, prec, out, workspace, workspace_bytes, as_stream(stream));
+  return ttgb::orth_left_enqueue(x, prec, out, workspace, workspace_bytes, as_stream(stream));
+}
+
 namespace {
 
 struct BatchStreams {

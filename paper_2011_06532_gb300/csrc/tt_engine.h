@@ -42,6 +42,15 @@ int tile_classes(const tt_tensor *x, int prec, int ctx, std::vector<TileKey> *ke
                  std::vector<TileChoice> *heuristic, std::vector<int64_t> *elems);
 int device_sm_count();
 int norm_workspace(const tt_tensor *x, size_t *bytes);
+int orth_workspace(const tt_tensor *x, int prec, size_t *bytes);
+int orth_enqueue(const tt_tensor *x, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st);
+int orth_left_workspace(const tt_tensor *x, int prec, size_t *bytes);
+int orth_left_enqueue(const tt_tensor *x, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st);
+int round_lrl_workspace(const tt_tensor *x, int prec, size_t *bytes);
+int round_hadamard_run(const tt_tensor *a, const tt_tensor *b, const tt_tensor *z, double eps, int prec,
+                       tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st);
+int round_lrl_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes,
+                  cudaStream_t st);
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st);
 
 int add_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStream_t st);

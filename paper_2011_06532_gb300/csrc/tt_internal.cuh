@@ -236,8 +236,8 @@ __device__ __forceinline__ int range_exp(double m) {
 template <typename T>
 struct Scratch {
   T *red;   // NT elements
-  T *wbuf;  // >= max columns elements
-  T *sc;    // 2 elements
+  T *wbuf;  // >= max columns elements (NT for hh_apply_grouped)
+  T *sc;    // 4 elements (two reflectors' scale and tau)
 };
 
 // H = I - tau u u^T with u = [1; v], v_r = V[r * ldv] for r in [r0, M), applied to the
@@ -319,217 +319,197 @@ __device__ __forceinline__ int tile_rows_for(int j, int M, int tri_off, int q = 
   return tri_off < 0 ? M : min(M, max(0, (j - tri_off + 1) * q));
 }
 
-template <typename T>
-__device__ int hh_factor_seq(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
-                         int tri_off = -1, int q = 1) {
-  const int kk = min(k + M, b);
-  // Narrow factors: warp 0 forms reflector j (column norm, square root, reciprocal) while
-  // the other warps apply the scaling still owed by the stored column of reflector pj
-  // (rows pr0..pM-1); then the whole CTA applies reflector j.
-  int pj = -1, pr0 = 0, pM = 0;
-  T pend = T(1);
-  for (int j = 0; j < kk; ++j) {
-    const int r0 = j < k ? 0 : j - k + 1;
-    const int Mj = tile_rows_for(j, M, tri_off, q);
-    T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
-    if (threadIdx.x >= 32 && pj >= 0) {
-      for (int r = pr0 + (int)threadIdx.x - 32; r < pM; r += NT - 32) tile[(size_t)r * ldt + pj] *= pend;
-    }
-    if (threadIdx.x < 32) {
-      T ss = T(0);
-      for (int r = r0 + threadIdx.x; r < Mj; r += 32) {
-        const T v = tile[(size_t)r * ldt + j];
-        ss += v * v;
-      }
-      ss = warp_sum(ss);
-      if (threadIdx.x == 0) {
-        T tj = T(0), scale = T(0);
-        if (ss != T(0)) {
-          const T alpha = piv[j];
-          const T v = alpha * alpha + ss;
-          const bool fast = std::is_same<T, double>::value && nr_range((double)v);
-          const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
-          const T beta = alpha >= T(0) ? -nrm : nrm;
-          const T d = alpha - beta;
-          const T bd = beta * d;
-          if (fast && nr_range(fabs((double)bd))) {
-            // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q
-            // and 1 / d = beta q
-            const T q = (T)rcp_nr((double)bd);
-            tj = -d * d * q;
-            scale = beta * q;
-          } else {
-            // textbook form; tau lies in [1, 2] whatever the scale of the column
-            tj = (beta - alpha) / beta;
-            scale = T(1) / d;
-          }
-          piv[j] = beta;
-        }
-        tau[j] = tj;
-        s.sc[0] = scale;
-        s.sc[1] = tj;
-      }
-    }
-    __syncthreads();
-    const T tj = s.sc[1];
-    pj = -1;
-    if (tj != T(0)) {
-      const T scale = s.sc[0];
-      reflect(tj, tile + j, ldt, r0, Mj, piv + j + 1, tile + j + 1, ldt, b - j - 1, s, scale);
-      pj = j;
-      pend = scale;
-      pr0 = r0;
-      pM = Mj;
-    } else {
-      __syncthreads();
-    }
-  }
-  if (pj >= 0) {
-    for (int r = pr0 + (int)threadIdx.x; r < pM; r += NT) tile[(size_t)r * ldt + pj] *= pend;
-  }
-  __syncthreads();
-  return kk;
+// Named CTA barriers (PTX bar.sync / bar.arrive with an id and a thread count; id 0 is
+// __syncthreads).  bar.arrive lets a warp signal a barrier without waiting at it.
+__device__ __forceinline__ void nbar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Scalars of one Householder reflector (LAPACK convention): from the pivot alpha and the
+// sum of squares ss of the entries below it, beta = -sign(alpha) sqrt(alpha^2 + ss),
+// tau = (beta - alpha) / beta and the scale 1 / (alpha - beta) of the stored column;
+// tau = 0 (identity) when ss = 0.
 template <typename T>
-__device__ int hh_factor_ahead(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
-                         int tri_off = -1, int q = 1) {
+__device__ __forceinline__ void house_scalars(T alpha, T ss, T &tj, T &scale, T &beta) {
+  tj = T(0);
+  scale = T(0);
+  beta = alpha;
+  if (ss == T(0)) return;
+  const T v = alpha * alpha + ss;
+  const bool fast = std::is_same<T, double>::value && nr_range((double)v);
+  const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
+  beta = alpha >= T(0) ? -nrm : nrm;
+  const T d = alpha - beta;
+  const T bd = beta * d;
+  if (fast && nr_range(fabs((double)bd))) {
+    // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q and 1 / d = beta q
+    const T qq = (T)rcp_nr((double)bd);
+    tj = -d * d * qq;
+    scale = beta * qq;
+  } else {
+    // textbook form; tau lies in [1, 2] whatever the scale of the column
+    tj = (beta - alpha) / beta;
+    scale = T(1) / d;
+  }
+}
+
+// Householder QR of the stacked matrix with look-ahead (layout and conventions as described
+// above).  Warp 0 forms the reflectors: while warps 1..7 take the dot products of
+// reflector j with the trailing columns and apply it to columns j+2.., warp 0 applies it
+// to column j+1 first, then computes the norm and the scalar chain (square root,
+// reciprocal) of reflector j+1, so that the ~30 dependent FP64 instructions of each chain
+// (each holding an SMSP's FP64 unit ~64 cycles on GB300) run beside the bulk work instead
+// of before it.  Named barriers: 1 among warps 1..7 (their reduction), 2 "scalars of the
+// next reflector ready" (warp 0 arrives), 3 "w ready" (all wait), 4 "column j+1 and all
+// updates done" (warp 0 arrives).  The stored column of reflector j is scaled by its
+// 1 / (alpha - beta) one step later, when nothing reads it any more.
+template <typename T>
+__device__ int hh_factor_la(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+                            int tri_off = -1, int q = 1) {
+  constexpr int NB = NT - 32;  // threads of warps 1..7
   const int kk = min(k + M, b);
   const int t = threadIdx.x;
-  // Wide factors: warp 0 forms reflector j (column norm, then the square root / reciprocal
-  // chain) while the other warps apply the scaling still owed by the stored column of
-  // reflector pj (rows pr0..pM-1) and already take the dot products of reflector j's
-  // unscaled column with the trailing columns (the scalars are needed only when w is
-  // formed).
-  const int nth = NT - 32;
-  int pj = -1, pr0 = 0, pM = 0;
-  T pend = T(1);
-  auto dots = [&](int u, int j, int r0, int Mj, int nc, int G) {
-    if (nc > 0 && u < G * nc) {
-      const int g = u / nc, c = u - g * nc;
-      const T *X = tile + j + 1 + c;
-      if constexpr (is_df<T>::value) {
-        float sh = 0.f, sl = 0.f;
-        for (int r = r0 + g; r < Mj; r += G) df_dot_acc(sh, sl, tile[(size_t)r * ldt + j], X[(size_t)r * ldt]);
-        s.red[g * nc + c] = df_finish(sh, sl);
-      } else {
-        T acc = T(0);
-        for (int r = r0 + g; r < Mj; r += G) acc += tile[(size_t)r * ldt + j] * X[(size_t)r * ldt];
-        s.red[g * nc + c] = acc;
-      }
+  const bool cw = t < 32;
+  const int u = t - 32;
+  auto pivrow = [&](int j) -> T * { return j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt; };
+  auto rows0 = [&](int j) { return j < k ? 0 : j - k + 1; };
+  // warp 0: scalars of reflector j from its (updated) column, published in slot j & 1
+  auto form = [&](int j) {
+    const int r0 = rows0(j), Mj = tile_rows_for(j, M, tri_off, q);
+    T ss = T(0);
+    for (int r = r0 + t; r < Mj; r += 32) {
+      const T v = tile[(size_t)r * ldt + j];
+      ss += v * v;
     }
+    ss = warp_sum(ss);
+    if (t == 0) {
+      T *piv = pivrow(j);
+      T tj, scale, beta;
+      house_scalars(piv[j], ss, tj, scale, beta);
+      piv[j] = beta;
+      tau[j] = tj;
+      s.sc[2 * (j & 1)] = scale;
+      s.sc[2 * (j & 1) + 1] = tj;
+    }
+    __syncwarp();
   };
-  for (int j = 0; j < kk; ++j) {
-    const int r0 = j < k ? 0 : j - k + 1;
-    const int Mj = tile_rows_for(j, M, tri_off, q);
-    T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
-    const int nc = b - j - 1, nrow = Mj - r0;
-    // dot-product groups over the nth threads taking them (nc < b <= TT_MAX_RANK < NT - 32)
-    int G = nc > 0 ? nth / nc : 1;
-    if (G > nrow) G = nrow > 0 ? nrow : 1;
-    if (t < 32) {
-      T ss = T(0);
-      for (int r = r0 + t; r < Mj; r += 32) {
-        const T v = tile[(size_t)r * ldt + j];
-        ss += v * v;
-      }
-      ss = warp_sum(ss);
-      if (t == 0) {
-        T tj = T(0), scale = T(0);
-        if (ss != T(0)) {
-          const T alpha = piv[j];
-          const T v = alpha * alpha + ss;
-          const bool fast = std::is_same<T, double>::value && nr_range((double)v);
-          const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
-          const T beta = alpha >= T(0) ? -nrm : nrm;
-          const T d = alpha - beta;
-          const T bd = beta * d;
-          if (fast && nr_range(fabs((double)bd))) {
-            // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q
-            // and 1 / d = beta q
-            const T qq = (T)rcp_nr((double)bd);
-            tj = -d * d * qq;
-            scale = beta * qq;
-          } else {
-            // textbook form; tau lies in [1, 2] whatever the scale of the column
-            tj = (beta - alpha) / beta;
-            scale = T(1) / d;
-          }
-          piv[j] = beta;
-        }
-        tau[j] = tj;
-        s.sc[0] = scale;
-        s.sc[1] = tj;
-      }
-    } else {
-      const int u = t - 32;
-      if (pj >= 0)
-        for (int r = pr0 + u; r < pM; r += NT - 32) tile[(size_t)r * ldt + pj] *= pend;
-      dots(u, j, r0, Mj, nc, G);
-    }
+  if (kk <= 0) {
     __syncthreads();
-    const T tj = s.sc[1];
-    pj = -1;
-    if (tj != T(0)) {
-      const T scale = s.sc[0];
+    return kk;
+  }
+  if (cw) {
+    form(0);
+    nbar_arrive(2, NT);
+  }
+  for (int j = 0; j < kk; ++j) {
+    const int r0 = rows0(j), Mj = tile_rows_for(j, M, tri_off, q);
+    const int nrow = Mj - r0;
+    const int nc = b - j - 1;
+    T *piv = pivrow(j);
+    if (!cw) {
+      // deferred scaling of reflector j-1's stored column (no one reads it any more)
+      if (j >= 1) {
+        const T sp = s.sc[2 * ((j - 1) & 1)];
+        const int pr0 = rows0(j - 1), pM = tile_rows_for(j - 1, M, tri_off, q);
+        for (int r = pr0 + u; r < pM; r += NB) tile[(size_t)r * ldt + j - 1] *= sp;
+      }
+      // dot products of the unscaled column j with the trailing columns (partials by row group)
+      int G = nc > 0 ? NB / nc : 1;
+      if (G > nrow) G = nrow > 0 ? nrow : 1;
+      if (nc > 0 && u < G * nc) {
+        const int g = u / nc, c = u - g * nc;
+        const T *X = tile + j + 1 + c;
+        if constexpr (is_df<T>::value) {
+          float sh = 0.f, sl = 0.f;
+          for (int r = r0 + g; r < Mj; r += G) df_dot_acc(sh, sl, tile[(size_t)r * ldt + j], X[(size_t)r * ldt]);
+          s.red[g * nc + c] = df_finish(sh, sl);
+        } else {
+          T acc = T(0);
+          for (int r = r0 + g; r < Mj; r += G) acc += tile[(size_t)r * ldt + j] * X[(size_t)r * ldt];
+          s.red[g * nc + c] = acc;
+        }
+      }
       if (nc > 0) {
+        nbar_sync(1, NB);
         for (int h = G; h > 1;) {
           const int half = (h + 1) >> 1;
-          for (int idx = t; idx < (h - half) * nc; idx += NT) s.red[idx] += s.red[idx + half * nc];
+          for (int idx = u; idx < (h - half) * nc; idx += NB) s.red[idx] += s.red[idx + half * nc];
           h = half;
-          __syncthreads();
+          nbar_sync(1, NB);
         }
+      }
+      nbar_sync(2, NT);  // scalars of reflector j
+      if (u < nc) {
+        const T scale = s.sc[2 * (j & 1)], tj = s.sc[2 * (j & 1) + 1];
         T *p = piv + j + 1;
-        if (t < nc) {
-          const T w = tj * (p[t] + scale * s.red[t]);
-          s.wbuf[t] = scale * w;
-          p[t] -= w;
-        }
-        __syncthreads();
-        if (nrow > 0) {
-          // dense walk over the nrow x nc trailing block: X -= v w^T (v unscaled, w scaled)
-          const int dq = NT / nc, dr = NT - dq * nc;
-          int r = t / nc, cc = t - (t / nc) * nc;
-          for (; r < nrow;) {
-            const size_t rr = (size_t)(r0 + r);
-            if constexpr (is_df<T>::value) {
-              T &x = tile[rr * ldt + j + 1 + cc];
-              x = df_sub_prod(x, tile[rr * ldt + j], s.wbuf[cc]);
-            } else {
-              tile[rr * ldt + j + 1 + cc] -= tile[rr * ldt + j] * s.wbuf[cc];
-            }
-            r += dq;
-            cc += dr;
-            if (cc >= nc) {
-              cc -= nc;
-              ++r;
-            }
+        const T w = tj * (p[u] + scale * s.red[u]);
+        s.wbuf[u] = scale * w;
+        p[u] -= w;
+      }
+      nbar_sync(3, NT);
+      // update columns j+2.. over the reflector's rows: X -= x_j w^T (x_j unscaled, w scaled)
+      const int ncu = nc - 1;
+      if (ncu > 0 && nrow > 0) {
+        const int dq = NB / ncu, dr = NB - dq * ncu;
+        int r = u / ncu, cc = u - (u / ncu) * ncu;
+        for (; r < nrow;) {
+          const size_t rr = (size_t)(r0 + r);
+          if constexpr (is_df<T>::value) {
+            T &x = tile[rr * ldt + j + 2 + cc];
+            x = df_sub_prod(x, tile[rr * ldt + j], s.wbuf[1 + cc]);
+          } else {
+            tile[rr * ldt + j + 2 + cc] -= tile[rr * ldt + j] * s.wbuf[1 + cc];
+          }
+          r += dq;
+          cc += dr;
+          if (cc >= ncu) {
+            cc -= ncu;
+            ++r;
           }
         }
       }
-      pj = j;
-      pend = scale;
-      pr0 = r0;
-      pM = Mj;
+      nbar_sync(4, NT);
+    } else {
+      nbar_sync(3, NT);
+      // column j+1 first
+      if (nc > 0) {
+        const T w1 = s.wbuf[0];
+        for (int r = r0 + t; r < Mj; r += 32) {
+          if constexpr (is_df<T>::value) {
+            T &x = tile[(size_t)r * ldt + j + 1];
+            x = df_sub_prod(x, tile[(size_t)r * ldt + j], w1);
+          } else {
+            tile[(size_t)r * ldt + j + 1] -= tile[(size_t)r * ldt + j] * w1;
+          }
+        }
+      }
+      __syncwarp();
+      nbar_arrive(4, NT);
+      if (j + 1 < kk) {
+        form(j + 1);
+        nbar_arrive(2, NT);
+      }
     }
-    __syncthreads();
   }
-  if (pj >= 0) {
-    for (int r = pr0 + t; r < pM; r += NT) tile[(size_t)r * ldt + pj] *= pend;
+  __syncthreads();
+  // the last reflector's stored column
+  {
+    const int j = kk - 1;
+    const T sp = s.sc[2 * (j & 1)];
+    for (int r = rows0(j) + t; r < tile_rows_for(j, M, tri_off, q); r += NT) tile[(size_t)r * ldt + j] *= sp;
   }
   __syncthreads();
   return kk;
 }
 
-// Householder QR of the stacked matrix (see above).  Factors of 48 or more columns take
-// reflector j's dot products while its scalars are being formed (hh_factor_ahead); narrower
-// ones measured faster with all threads on the dot products after the scalars
-// (hh_factor_seq), as that spreads fewer products per reflector over more threads.
+// Householder QR of the stacked matrix (see above): the look-ahead form.
 template <typename T>
 __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
                          int tri_off = -1, int q = 1) {
-  return b >= 48 ? hh_factor_ahead(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q)
-                 : hh_factor_seq(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q);
+  return hh_factor_la(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q);
 }
 
 // Moves the new R rows k..kk-1 produced by hh_factor from the tile into Rr (zeroing the
@@ -558,6 +538,175 @@ __device__ void hh_apply(const T *V, int ldv, const T *tau, int k, int M, int b,
     const int r0 = j < k ? 0 : j - k + 1;
     T *piv = j < k ? CR + (size_t)j * ldcr : CT + (size_t)(j - k) * ldct;
     reflect(tj, V + j, ldv, r0, tile_rows_for(j, M, tri_off, q), piv, CT, ldct, nc, s);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Grouped application of one dense tile's reflectors (compact WY form)
+// ------------------------------------------------------------------------------------
+// The product of g consecutive reflectors H_{j0} ... H_{j0+g-1} is I - U T U^T with
+// U = [u_{j0} .. u_{j0+g-1}] and T upper triangular: T_ii = tau_i,
+// T(0:i, i) = -tau_i T(0:i, 0:i) U(:, 0:i)^T u_i (the forward accumulation of Schreiber
+// and Van Loan, "A storage-efficient WY representation for products of Householder
+// transformations", SIAM J. Sci. Stat. Comput. 1989).  Applying the group is then
+// C <- C - U (T (U^T C)): one set of dot products, one reduction and one update per g
+// reflectors instead of per reflector, which removes most of the CTA barriers and the
+// partial-warp reductions that leave the FP64 pipe idle in the reflector-by-reflector
+// form.  Reflector j of the tile has its unit pivot in CR row j (j < k) or tile row
+// j - k, and stored entries V(r, j) on tile rows r > j - k (all rows when j < k).
+
+// group size for C blocks of nc columns: g * nc dot products must fit the CTA
+__device__ __host__ __forceinline__ int apply_group(int nc) {
+  const int g = nc > 0 ? NT / nc : 4;
+  return g >= 4 ? 4 : (g < 1 ? 1 : g);
+}
+// entries of the per-tile T storage (upper triangles of the groups' T), for b reflectors
+__device__ __host__ __forceinline__ int apply_tstore(int b) { return ((b + 1) / 2) * 10 + 10; }
+
+template <typename T>
+__device__ __forceinline__ T refl_entry(const T *V, int ldv, int k, int j, int r) {
+  if (j < k) return V[(size_t)r * ldv + j];
+  const int pr = j - k;
+  return r > pr ? V[(size_t)r * ldv + j] : (r == pr ? T(1) : T(0));
+}
+
+// index of T(a, b) (a <= b < 4) in a group's packed upper triangle
+__device__ __forceinline__ int tri_idx(int a, int b) { return a + (b * (b + 1)) / 2; }
+
+// Q_t [CR; CT] for the reflectors of one hh_factor step on a dense tile (see hh_apply);
+// Tst: shared scratch of apply_tstore(b) elements; s.wbuf must hold NT elements.
+template <typename T>
+__device__ void hh_apply_grouped(const T *V, int ldv, const T *tau, int k, int M, int b, T *CR, int ldcr, T *CT,
+                                 int ldct, int nc, Scratch<T> s, T *Tst) {
+  const int kk = min(k + M, b);
+  if (kk <= 0 || nc <= 0) return;
+  const int t = threadIdx.x;
+  const int g = apply_group(nc);
+  const int ng = (kk + g - 1) / g;
+  // (1) Gram entries u_a^T u_b (a < b) of every group, as dot products over tile rows
+  //     from u_b's pivot down (CR rows hold only pivots, which never overlap)
+  const int npair = (g * (g - 1)) / 2;
+  const int nout = ng * npair;
+  if (nout > 0) {
+    const int Gr = max(1, NT / nout);
+    if (t < Gr * nout) {
+      const int o = t % nout, gr = t / nout;
+      const int gi = o / npair, pi = o - gi * npair;
+      // pair index pi -> (a, b), a < b
+      int a = 0, bb = 1, cnt = pi;
+      while (cnt >= bb) {
+        cnt -= bb;
+        ++bb;
+      }
+      a = cnt;
+      const int ja = gi * g + a, jb = gi * g + bb;
+      T acc = T(0);
+      if (jb < kk) {
+        const int start = jb < k ? 0 : jb - k;
+        if constexpr (is_df<T>::value) {
+          float sh = 0.f, sl = 0.f;
+          for (int r = start + gr; r < M; r += Gr)
+            df_dot_acc(sh, sl, refl_entry(V, ldv, k, ja, r), refl_entry(V, ldv, k, jb, r));
+          acc = df_finish(sh, sl);
+        } else {
+          for (int r = start + gr; r < M; r += Gr) acc += refl_entry(V, ldv, k, ja, r) * refl_entry(V, ldv, k, jb, r);
+        }
+      }
+      s.red[gr * nout + o] = acc;
+    }
+    __syncthreads();
+    if (t < nout) {
+      const int Gr = max(1, NT / nout);
+      T sum = s.red[t];
+      for (int gr = 1; gr < Gr; ++gr) sum += s.red[gr * nout + t];
+      s.red[t] = sum;
+    }
+    __syncthreads();
+  }
+  // (2) T of every group (one thread per group), packed upper triangles of 10 entries
+  for (int gi = t; gi < ng; gi += NT) {
+    T *Tg = Tst + gi * 10;
+    const T *Gp = s.red + gi * npair;
+    const int gs = min(g, kk - gi * g);
+    for (int i = 0; i < gs; ++i) {
+      const T ti = tau[gi * g + i];
+      Tg[tri_idx(i, i)] = ti;
+      for (int a = 0; a < i; ++a) {
+        // T(a, i) = -tau_i sum_{a <= c < i} T(a, c) G(c, i)
+        T acc = T(0);
+        for (int c = a; c < i; ++c) acc += Tg[tri_idx(a, c)] * Gp[tri_idx(c, i) - i];
+        Tg[tri_idx(a, i)] = -(ti * acc);
+      }
+    }
+  }
+  __syncthreads();
+  // (3) groups from the last to the first (Q_t = H_0 ... H_{kk-1} acts on C from the right end)
+  for (int gi = ng - 1; gi >= 0; --gi) {
+    const int j0 = gi * g, gs = min(g, kk - j0);
+    const int nd = gs * nc;
+    const int Gr = max(1, NT / nd);
+    const T *Tg = Tst + gi * 10;
+    // (3a) D = U^T C: output o = (i, c), row groups gr
+    if (t < Gr * nd) {
+      const int o = t % nd, gr = t / nd;
+      const int i = o % gs, c = o / gs;
+      const int j = j0 + i;
+      const int start = j < k ? 0 : j - k;
+      T acc = T(0);
+      if constexpr (is_df<T>::value) {
+        float sh = 0.f, sl = 0.f;
+        for (int r = start + gr; r < M; r += Gr)
+          df_dot_acc(sh, sl, refl_entry(V, ldv, k, j, r), CT[(size_t)r * ldct + c]);
+        acc = df_finish(sh, sl);
+      } else {
+        for (int r = start + gr; r < M; r += Gr) acc += refl_entry(V, ldv, k, j, r) * CT[(size_t)r * ldct + c];
+      }
+      if (gr == 0 && j < k) acc += CR[(size_t)j * ldcr + c];
+      s.red[gr * nd + o] = acc;
+    }
+    __syncthreads();
+    // (3b) W = T D: thread (i, c) sums the partials of D(i'..gs-1, c) it needs
+    if (t < nd) {
+      const int i = t % gs, c = t / gs;
+      T w = T(0);
+      for (int i2 = i; i2 < gs; ++i2) {
+        const int o2 = i2 + gs * c;
+        T d = s.red[o2];
+        for (int gr = 1; gr < Gr; ++gr) d += s.red[gr * nd + o2];
+        w += Tg[tri_idx(i, i2)] * d;
+      }
+      s.wbuf[t] = w;
+    }
+    __syncthreads();
+    // (3c) C -= U W
+    if (t < nd) {
+      const int i = t % gs, c = t / gs;
+      if (j0 + i < k) CR[(size_t)(j0 + i) * ldcr + c] -= s.wbuf[t];
+    }
+    {
+      const int rstart = j0 < k ? 0 : j0 - k;
+      const int q = NT / nc;  // threads per column
+      if (t < q * nc) {
+        const int c = t % nc;
+        const T w0 = s.wbuf[gs * c], w1 = gs > 1 ? s.wbuf[1 + gs * c] : T(0);
+        const T w2 = gs > 2 ? s.wbuf[2 + gs * c] : T(0), w3 = gs > 3 ? s.wbuf[3 + gs * c] : T(0);
+        auto sub = [](T x, T v, T w) -> T {
+          if constexpr (is_df<T>::value)
+            return df_sub_prod(x, v, w);
+          else
+            return x - v * w;
+        };
+        for (int r = rstart + t / nc; r < M; r += q) {
+          T x = CT[(size_t)r * ldct + c];
+          x = sub(x, refl_entry(V, ldv, k, j0, r), w0);
+          if (gs > 1) x = sub(x, refl_entry(V, ldv, k, j0 + 1, r), w1);
+          if (gs > 2) x = sub(x, refl_entry(V, ldv, k, j0 + 2, r), w2);
+          if (gs > 3) x = sub(x, refl_entry(V, ldv, k, j0 + 3, r), w3);
+          CT[(size_t)r * ldct + c] = x;
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 

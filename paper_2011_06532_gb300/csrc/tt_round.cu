@@ -38,9 +38,35 @@ struct Geom {
   int Tt;     // slices per tile
 };
 
+// Source of an input core's entries (a, i, c): a stored core (R0 x I x R1, entry at
+// a + R0 (i + I c)), or the Hadamard product of two stored cores A_n, B_n (Sec. 3.2.2)
+// formed on the fly, so that the rounding of A o B never writes or reads the
+// R_A R_B x I x R_A' R_B' product: row a = p Rb + q and column c = s Rb' + t of slice i
+// give A_n(p, i, s) B_n(q, i, t).
+template <typename S>
+struct CoreSrc {
+  const S *X = nullptr;  // the core, or A_n
+  const S *B = nullptr;  // B_n (Hadamard), else nullptr
+  int R0 = 1;            // left rank of the (product) core
+  int ra0 = 1, rb0 = 1, rb1 = 1;
+  int64_t I = 1;
+};
+
+template <typename T, typename S>
+__device__ __forceinline__ T src_load(const CoreSrc<S> &s, int64_t a, int64_t i, int64_t c) {
+  if (!s.B) return T(s.X[(size_t)a + (size_t)s.R0 * ((size_t)i + (size_t)s.I * c)]);
+  const int64_t p = a / s.rb0, q = a - p * s.rb0, sa = c / s.rb1, tb = c - sa * s.rb1;
+  const S va = s.X[(size_t)p + (size_t)s.ra0 * ((size_t)i + (size_t)s.I * sa)];
+  const S vb = s.B[(size_t)q + (size_t)s.rb0 * ((size_t)i + (size_t)s.I * tb)];
+  if constexpr (std::is_same<T, float>::value)
+    return va * vb;
+  else
+    return T((double)va * (double)vb);  // exact for FP32 factors (held as a double-float pair)
+}
+
 template <typename S, typename T>
 struct S1Args {
-  const S *X;  // core n: b x I x cin
+  CoreSrc<S> X;  // core n: b x I x cin
   Geom g;
   int b, cin, rho;   // columns (R_n), right rank of X (R_{n+1}), rows per slice (K_{n+1})
   const double *Pm;  // rho x cin row-major (upper trapezoidal), nullptr = identity (rho == cin == 1)
@@ -80,7 +106,8 @@ struct TreeArgs {
 template <typename S, typename T>
 struct S2Args {
   // mode A (core n >= 1): apply stored sweep-1 Q_n to C; mode B (core 0): push X_0
-  int mode;       // 0 = A, 1 = B, 2 = last core (mode A, write output, no V-QR)
+  int mode;       // 0 = A, 1 = B, 2 = last core (mode A, write output, no V-QR),
+                  // 3 = explicit orthonormal factor (mode 2 for any K1, unscaled)
   Geom g;
   // mode A
   const T *qrefl;       // (I*K1) x b1 (sweep-1 reflectors)
@@ -91,7 +118,7 @@ struct S2Args {
   int ldc;
   const int *Lcur;      // &L[n]: columns of C = rows per slice of V(Y_n)
   // mode B
-  const S *X0;          // core 0: 1 x I x cin
+  CoreSrc<S> X0;        // core 0: 1 x I x cin
   int cin;
   const double *Pm;     // K1 x cin
   int CC;
@@ -102,7 +129,7 @@ struct S2Args {
   S *out;               // last core output (L x I x 1)
   const int *E;         // exponent gathered by the sweep-1 rescaling (see out_scale)
   int n, N;             // index of the core written, number of cores
-  int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv;
+  int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv, oTs;
   int ldq, ldv;
   T *gscr;
   size_t gstride;
@@ -121,7 +148,7 @@ struct OutArgs {
   S *out;               // output core n: L[n] x I x L[n+1]
   const int *E;         // exponent gathered by the sweep-1 rescaling (see out_scale)
   int n, N;
-  int oV, oCT, oCR, oRed, oW, oSc, oTau;
+  int oV, oCT, oCR, oRed, oW, oSc, oTau, oTs;
   int ldv;
   T *gscr;
   size_t gstride;
@@ -205,7 +232,7 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
       // rho == cin == 1: the tile rows are the slices themselves
       for (int idx = t; idx < M * b; idx += NT) {
         const int r = idx / b, c = idx - r * b;
-        tile[r * ldt + c] = T(a.X[(size_t)(i0 + r) * b + c]);
+        tile[r * ldt + c] = src_load<T>(a.X, c, i0 + r, 0);
       }
     } else {
       for (int idx = t; idx < M * b; idx += NT) {
@@ -218,7 +245,8 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
         const int chunk = nt * b;
         for (int idx = t; idx < cc_n * chunk; idx += NT) {
           const int cc = idx / chunk, rem = idx - cc * chunk;
-          Xs[idx] = T(a.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem]);
+          const int il = rem / b;
+          Xs[idx] = src_load<T>(a.X, rem - il * b, i0 + il, c0 + cc);
         }
         __syncthreads();
         // one copy of the loop per place the factor is read from (FP64 global, staged
@@ -495,7 +523,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   T *Q = sm<T>(smem, a.oQ), *CT = sm<T>(smem, a.oCT);
   T *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride), *Rr = buf<T>(smem, a.oRr, a.gscr, a.gstride);
   T *Xs = sm<T>(smem, a.oXs), *Ps = buf<T>(smem, a.oPs, a.gscr, a.gstride);
-  Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
+  Scratch<T> s{sm<T>(smem, a.oRed), buf<T>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
   T *tq = sm<T>(smem, a.oTq), *tv = sm<T>(smem, a.oTv);
   const int p = blockIdx.x, t = threadIdx.x;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
@@ -540,13 +568,15 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
         CT[idx] = (kb + r < ka) ? CR[(kb + r) * L + c] : T(0);
       }
       __syncthreads();
-      hh_apply(Q, a.ldq, tq, kb, M1, b1, CR, L, CT, L, L, s);
+      hh_apply_grouped(Q, a.ldq, tq, kb, M1, b1, CR, L, CT, L, L, s, buf<T>(smem, a.oTs, a.gscr, a.gstride));
       __syncthreads();
-      if (a.mode == 2) {
-        // last core: Y[l, i, 0] = CT[(i - i0)][l]  (K1 == 1)
-        for (int idx = t; idx < nt * L; idx += NT) {
-          const int il = idx / L, l = idx - il * L;
-          a.out[(size_t)l + (size_t)L * (i0 + il)] = (S)CT[il * L + l] * osc;
+      if (a.mode >= 2) {
+        // last core (K1 == 1) or an explicit orthonormal factor: tile row (i - i0) K1 + k
+        // of Q_n [C_p; 0] is row (i, k) of H(Y_n)^T, so Y[l, i, k] = CT[(i - i0) K1 + k][l]
+        for (int idx = t; idx < nt * K1 * L; idx += NT) {
+          const int r = idx / L, l = idx - r * L;
+          const int il = r / K1, k = r - il * K1;
+          a.out[(size_t)l + (size_t)L * ((i0 + il) + a.g.I * (int64_t)k)] = (S)CT[r * L + l] * osc;
         }
         __syncthreads();
         continue;
@@ -566,7 +596,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
         __syncthreads();
         for (int idx = t; idx < cc_n * nt; idx += NT) {
           const int cc = idx / nt, il = idx - cc * nt;
-          Xs[idx] = T(a.X0[(size_t)(i0 + il) + (size_t)a.g.I * (c0 + cc)]);
+          Xs[idx] = src_load<T>(a.X0, 0, i0 + il, c0 + cc);
         }
         __syncthreads();
         for (int idx = t; idx < Mv * K1; idx += NT) {
@@ -589,7 +619,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
     hh_take_rows(Rr, K1, kv, kk, Q, a.ldv, K1);
     kv = kk;
   }
-  if (a.mode == 2) return;
+  if (a.mode >= 2) return;
   double *Ro = a.Rleaf + (size_t)p * K1 * K1;
   for (int idx = t; idx < K1 * K1; idx += NT) Ro[idx] = (idx / K1) < kv ? (double)Rr[idx] : 0.0;
 }
@@ -602,7 +632,7 @@ template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   T *V = sm<T>(smem, a.oV), *CT = sm<T>(smem, a.oCT), *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride);
-  Scratch<T> s{sm<T>(smem, a.oRed), sm<T>(smem, a.oW), sm<T>(smem, a.oSc)};
+  Scratch<T> s{sm<T>(smem, a.oRed), buf<T>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
   T *tv = sm<T>(smem, a.oTau);
   const int p = blockIdx.x, t = threadIdx.x;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
@@ -632,7 +662,7 @@ __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
       CT[idx] = (kb + r < ka) ? CR[(kb + r) * Ln + c] : T(0);
     }
     __syncthreads();
-    hh_apply(V, a.ldv, tv, kb, Mv, K1, CR, Ln, CT, Ln, Ln, s);
+    hh_apply_grouped(V, a.ldv, tv, kb, Mv, K1, CR, Ln, CT, Ln, Ln, s, buf<T>(smem, a.oTs, a.gscr, a.gstride));
     __syncthreads();
     // rows (i - i0) * L + l, column l'  ->  out[l + L (i + I l')]
     for (int idx = t; idx < Mv * Ln; idx += NT) {
@@ -1012,6 +1042,34 @@ __global__ void __launch_bounds__(NT) k_push_sumsq(const T *X0, int64_t I, int c
   }
 }
 
+// First core of an orthonormalized tensor: Y_0 = 2^E X_0 x_3 P (P = K x cin upper trapezoidal,
+// row-major with leading dimension cin: the root factor pushed from core 1, Alg. 1).
+template <typename S>
+__global__ void __launch_bounds__(NT) k_push_out(const S *X0, int64_t I, int cin, int K, const double *Pm,
+                                                 const int *E, S *out) {
+  const int64_t total = I * K;
+  const double sc = ldexp(1.0, *E);
+  for (int64_t e = (int64_t)blockIdx.x * NT + threadIdx.x; e < total; e += (int64_t)gridDim.x * NT) {
+    const int kk = (int)(e / I);
+    const int64_t i = e - (int64_t)kk * I;
+    double v = 0.0;
+    for (int c = kk; c < cin; ++c) v += (double)X0[i + I * c] * Pm[kk * cin + c];
+    out[e] = (S)(v * sc);
+  }
+}
+
+// C <- identity (k x k, row-major with leading dimension ld)
+__global__ void k_eye(double *C, int k, int ld) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < k * k; idx += gridDim.x * blockDim.x) {
+    const int r = idx / k, c = idx - r * k;
+    C[(size_t)r * ld + c] = r == c ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_set_int(int *p, int v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
 __global__ void k_init_ctl(int *L, int N, int *status) {
   for (int i = threadIdx.x; i <= N; i += blockDim.x) L[i] = 1;
   if (threadIdx.x < 4) status[threadIdx.x] = 0;
@@ -1147,7 +1205,7 @@ SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false, b
               : (int)c.take(16);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(b, 1));
-  m.oSc = (int)c.take(sizeof(T) * 2);
+  m.oSc = (int)c.take(sizeof(T) * 4);  // reflector scalars, double-buffered (hh_factor_la)
   m.oTau = (int)c.take(sizeof(T) * b);
   m.bytes = c.off;
   m.gstride = pl.g;
@@ -1156,7 +1214,7 @@ SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false, b
 
 template <typename T>
 struct SmemS2 {
-  int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv, ldq, ldv;
+  int oQ, oCT, oCR, oRr, oXs, oPs, oRed, oW, oSc, oTq, oTv, oTs, ldq, ldv;
   size_t bytes, gstride;
 };
 
@@ -1178,8 +1236,12 @@ SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC, b
   m.oXs = (int)c.take(sizeof(T) * (mode == 1 ? (size_t)CC * Tt : 1));
   m.oPs = pl.take(sizeof(T) * (mode == 1 ? (size_t)K1 * cin : 1), mode == 1 ? (size_t)K1 * cin : 1, true);
   m.oRed = (int)c.take(sizeof(T) * NT);
-  m.oW = (int)c.take(sizeof(T) * std::max(std::max(b1, K1), Lmax));
-  m.oSc = (int)c.take(sizeof(T) * 2);
+  // the grouped apply's W and T store go to the per-leaf global scratch with the other
+  // spilled buffers when a core's buffers do not fit in shared memory
+  const size_t nw = (size_t)std::max(std::max(std::max(b1, K1), Lmax), NT);
+  m.oW = pl.take(sizeof(T) * nw, nw, true);
+  m.oTs = pl.take(sizeof(T) * apply_tstore(std::max(b1, 1)), (size_t)apply_tstore(std::max(b1, 1)), true);
+  m.oSc = (int)c.take(sizeof(T) * 4);  // reflector scalars, double-buffered (hh_factor_la)
   m.oTq = (int)c.take(sizeof(T) * std::max(b1, 1));
   m.oTv = (int)c.take(sizeof(T) * K1);
   m.bytes = c.off;
@@ -1189,7 +1251,7 @@ SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC, b
 
 template <typename T>
 struct SmemOut {
-  int oV, oCT, oCR, oRed, oW, oSc, oTau, ldv;
+  int oV, oCT, oCR, oRed, oW, oSc, oTau, oTs, ldv;
   size_t bytes, gstride;
 };
 
@@ -1203,8 +1265,10 @@ SmemOut<T> smem_out(int K1, int Lmax, int Tt, bool spill = false) {
   m.oCT = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * K1);
   m.oCR = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, true);
   m.oRed = (int)c.take(sizeof(T) * NT);
-  m.oW = (int)c.take(sizeof(T) * std::max(K1, 1));
-  m.oSc = (int)c.take(sizeof(T) * 2);
+  const size_t nw = (size_t)std::max(K1, NT);
+  m.oW = pl.take(sizeof(T) * nw, nw, true);
+  m.oTs = pl.take(sizeof(T) * apply_tstore(std::max(K1, 1)), (size_t)apply_tstore(std::max(K1, 1)), true);
+  m.oSc = (int)c.take(sizeof(T) * 4);  // reflector scalars, double-buffered (hh_factor_la)
   m.oTau = (int)c.take(sizeof(T) * K1);
   m.bytes = c.off;
   m.gstride = pl.g;
@@ -1230,7 +1294,7 @@ static size_t tree_bytes(int b, int MT, int w, SmemTree *m) {
   const int oB = (int)c.take(((size_t)MT * (b + 1) + (size_t)MT * w) * sizeof(double));
   const int oRed = (int)c.take(sizeof(double) * NT);
   const int oW = (int)c.take(sizeof(double) * std::max(b, w));
-  const int oSc = (int)c.take(sizeof(double) * 2);
+  const int oSc = (int)c.take(sizeof(double) * 4);
   const int oTau = (int)c.take(sizeof(double) * b);
   if (m) {
     m->lda = b + 1;
@@ -1635,8 +1699,26 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
   return TT_OK;
 }
 
+// Source of core n of x, or of the Hadamard product of x and xb when xb is given.
+template <typename S>
+static CoreSrc<S> core_src(const tt_tensor *x, const tt_tensor *xb, int n) {
+  CoreSrc<S> c;
+  c.X = reinterpret_cast<const S *>(x->cores[n]);
+  c.I = x->I[n];
+  c.R0 = (int)x->R[n];
+  if (xb) {
+    c.B = reinterpret_cast<const S *>(xb->cores[n]);
+    c.ra0 = (int)x->R[n];
+    c.rb0 = (int)xb->R[n];
+    c.rb1 = (int)xb->R[n + 1];
+    c.R0 = c.ra0 * c.rb0;
+  }
+  return c;
+}
+
 template <typename S, typename T>
-static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st, int *E) {
+static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st, int *E,
+                  const tt_tensor *xb = nullptr) {
   const int N = pl.N;
   const int B = pl.bmax;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
@@ -1650,7 +1732,7 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     S1Args<S, T> a{};
     a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
     a.gstride = m.gstride;
-    a.X = reinterpret_cast<const S *>(x->cores[n]);
+    a.X = core_src<S>(x, xb, n);
     a.g = Geom{c.I, c.P, c.Tt};
     a.b = c.R0;
     a.cin = c.R1;
@@ -1702,7 +1784,8 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
 // word to status_dev, device side, and returns without a host synchronization.
 template <typename S, typename T>
 static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_tensor *out, unsigned char *ws,
-                     cudaStream_t st, int *ranks_dev = nullptr, int *status_dev = nullptr) {
+                     cudaStream_t st, int *ranks_dev = nullptr, int *status_dev = nullptr,
+                     const tt_tensor *xb = nullptr) {
   const int N = pl.N;
   const int B = pl.bmax;
   int *dL = reinterpret_cast<int *>(ws + pl.off_L);
@@ -1715,7 +1798,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   }
   TT_CUDA(cudaGetLastError());
   int *dE = dstatus + 2;  // exponent of the sweep-1 rescaling (zeroed above)
-  int r = sweep1<S, T>(pl, x, ws, st, dE);
+  int r = sweep1<S, T>(pl, x, ws, st, dE, xb);
   if (r) return r;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
   double *C1 = reinterpret_cast<double *>(ws + pl.off_C1);
@@ -1752,7 +1835,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
         a.Lcur = dL + n;
       } else {
         a.b1 = 1;
-        a.X0 = reinterpret_cast<const S *>(x->cores[0]);
+        a.X0 = core_src<S>(x, xb, 0);
         a.cin = c.R1;
         a.Pm = N > 1 ? P1 : nullptr;
         a.CC = 8;
@@ -1769,6 +1852,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.oPs = m.oPs;
       a.oRed = m.oRed;
       a.oW = m.oW;
+      a.oTs = m.oTs;
       a.oSc = m.oSc;
       a.oTq = m.oTq;
       a.oTv = m.oTv;
@@ -1838,6 +1922,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.oCR = m.oCR;
       a.oRed = m.oRed;
       a.oW = m.oW;
+      a.oTs = m.oTs;
       a.oSc = m.oSc;
       a.oTau = m.oTau;
       a.ldv = m.ldv;
@@ -1881,6 +1966,7 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     a.oPs = m.oPs;
     a.oRed = m.oRed;
     a.oW = m.oW;
+    a.oTs = m.oTs;
     a.oSc = m.oSc;
     a.oTq = m.oTq;
     a.oTv = m.oTv;
@@ -1946,6 +2032,22 @@ int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws
   return round_enqueue(x, eps, prec, out, ws, ws_bytes, st, nullptr, nullptr);
 }
 
+// Rounding of the Hadamard product z = a o b (shape of the product in z) without forming
+// it: the leaf kernels read the entries of a and b (see CoreSrc); ranks to out->R.
+int round_hadamard_run(const tt_tensor *a, const tt_tensor *b, const tt_tensor *z, double eps, int prec,
+                       tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+  RoundPlan pl;
+  int r = plan_for(z, prec, pl, false, kCtxSolo);
+  if (r) return r;
+  if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
+  unsigned char *w = reinterpret_cast<unsigned char *>(ws);
+  switch (prec) {
+    case TT_PREC_FP64: return run_round<double, double>(pl, a, eps, out, w, st, nullptr, nullptr, b);
+    case TT_PREC_FP32X2: return run_round<float, df32>(pl, a, eps, out, w, st, nullptr, nullptr, b);
+    default: return run_round<float, float>(pl, a, eps, out, w, st, nullptr, nullptr, b);
+  }
+}
+
 static int norm_prec(const tt_tensor *x) { return x->dtype == TT_F64 ? TT_PREC_FP64 : TT_PREC_FP32X2; }
 
 int norm_workspace(const tt_tensor *x, size_t *bytes) {
@@ -1984,6 +2086,122 @@ static int run_norm(const RoundPlan &pl, const tt_tensor *x, double *result, uns
   TT_CUDA(cudaMemcpyAsync(result, res, sizeof(double), cudaMemcpyDeviceToHost, st));
   TT_CUDA(cudaStreamSynchronize(st));
   return TT_OK;
+}
+
+// Right-orthonormalization with explicit factors (Alg. 5: TSQR of every H(X_n)^T, then
+// TSQR-Apply-Q of the identity to form the orthonormal factor, R pushed into core n-1).
+// Sweep 1 of the rounding leaves every core's reflectors stored; each core n >= 1 then
+// gets Q_n [I; 0] through its tree and leaves (k_s2_leaf in the explicit-factor mode),
+// and core 0 receives the pushed root factor.  Ranks K_n = min(R_n, I_n K_{n+1}) follow
+// from the shapes, so nothing waits on the device.
+template <typename S, typename T>
+static int run_orth(const RoundPlan &pl, const tt_tensor *x, tt_tensor *out, unsigned char *ws, cudaStream_t st) {
+  const int N = pl.N;
+  const int B = pl.bmax;
+  int *dL = reinterpret_cast<int *>(ws + pl.off_L);
+  int *dstatus = reinterpret_cast<int *>(ws + pl.off_status);
+  {
+    TraceScope ts_(TT_K_MISC, st);
+    k_init_ctl<<<1, 32, 0, st>>>(dL, N, dstatus);
+  }
+  TT_CUDA(cudaGetLastError());
+  int *dE = dstatus + 2;
+  int r = sweep1<S, T>(pl, x, ws, st, dE);
+  if (r) return r;
+  double *C1 = reinterpret_cast<double *>(ws + pl.off_C1);
+  for (int n = 1; n < N; ++n) {
+    const CorePlan &c = pl.core[n];
+    {
+      TraceScope ts_(TT_K_MISC, st);
+      k_set_int<<<1, 32, 0, st>>>(dL + n, c.K0);
+      k_eye<<<std::max(1, (c.K0 * c.K0 + 255) / 256), 256, 0, st>>>(C1 + c.tree.node_off[c.tree.nlev] * (size_t)B * B,
+                                                                     c.K0, B);
+    }
+    TT_CUDA(cudaGetLastError());
+    r = tree_apply(c.tree, c.R0, c.I, c.K1, nullptr, c.K0, nullptr, c.K0, C1,
+                   reinterpret_cast<double *>(ws + c.slot_off), B, st);
+    if (r) return r;
+    const SmemS2<T> m = smem_s2<T>(2, c.R0, c.K1, c.K0, c.Tt, 1, 8, c.spill);
+    S2Args<S, T> a{};
+    a.gscr = reinterpret_cast<T *>(ws + pl.off_gscr);
+    a.gstride = m.gstride;
+    a.mode = 3;
+    a.g = Geom{c.I, c.P, c.Tt};
+    a.qrefl = reinterpret_cast<const T *>(ws + c.refl_off);
+    a.qtau = reinterpret_cast<const T *>(ws + c.tau_off);
+    a.b1 = c.R0;
+    a.K1 = c.K1;
+    a.Cleaf = C1 + c.tree.node_off[0] * (size_t)B * B;
+    a.ldc = B;
+    a.Lcur = dL + n;
+    a.out = reinterpret_cast<S *>(out->cores[n]);
+    a.E = dE;
+    a.n = n;
+    a.N = N;
+    a.oQ = m.oQ;
+    a.oCT = m.oCT;
+    a.oCR = m.oCR;
+    a.oRr = m.oRr;
+    a.oXs = m.oXs;
+    a.oPs = m.oPs;
+    a.oRed = m.oRed;
+    a.oW = m.oW;
+    a.oTs = m.oTs;
+    a.oSc = m.oSc;
+    a.oTq = m.oTq;
+    a.oTv = m.oTv;
+    a.ldq = m.ldq;
+    a.ldv = m.ldv;
+    r = set_smem(k_s2_leaf<S, T>, m.bytes);
+    if (r) return r;
+    {
+      TraceScope ts_(TT_K_S2_LEAF, st);
+      k_s2_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
+    }
+    TT_CUDA(cudaGetLastError());
+  }
+  // core 0: X_0 x_3 R_1 (the root factor of core 1, kept at off_P), times 2^E
+  {
+    const CorePlan &c0 = pl.core[0];
+    const int64_t total = c0.I * c0.K1;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (total + NT - 1) / NT));
+    TraceScope ts_(TT_K_MISC, st);
+    k_push_out<S><<<blocks, NT, 0, st>>>(reinterpret_cast<const S *>(x->cores[0]), c0.I, c0.R1, c0.K1,
+                                          reinterpret_cast<const double *>(ws + pl.off_P), dE,
+                                          reinterpret_cast<S *>(out->cores[0]));
+  }
+  TT_CUDA(cudaGetLastError());
+  out->R[0] = 1;
+  for (int n = 1; n < N; ++n) out->R[n] = pl.core[n].K0;
+  out->R[N] = 1;
+  return TT_OK;
+}
+
+int orth_workspace(const tt_tensor *x, int prec, size_t *bytes) {
+  if (x->N == 1) {
+    *bytes = 0;
+    return TT_OK;
+  }
+  return round_workspace(x, prec, bytes);
+}
+
+int orth_enqueue(const tt_tensor *x, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+  if (x->N == 1) {
+    const size_t es = x->dtype == TT_F64 ? 8 : 4;
+    TT_CUDA(cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDefault, st));
+    out->R[0] = out->R[1] = 1;
+    return TT_OK;
+  }
+  RoundPlan pl;
+  int r = plan_for(x, prec, pl, false);
+  if (r) return r;
+  if (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)) return TT_ERR_WORKSPACE;
+  unsigned char *w = reinterpret_cast<unsigned char *>(ws);
+  switch (prec) {
+    case TT_PREC_FP64: return run_orth<double, double>(pl, x, out, w, st);
+    case TT_PREC_FP32X2: return run_orth<float, df32>(pl, x, out, w, st);
+    default: return run_orth<float, float>(pl, x, out, w, st);
+  }
 }
 
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st) {

@@ -23,7 +23,7 @@ import numpy as np
 
 LARGE_MODES = dict(I=65536, N=10, r=16, seed=2011065302, eps=1e-8)
 MODEL1 = dict(I=2000, N=50, r=25, seed=2011065306)
-DECAYING = dict(I=2048, N=50, seed=2011065303, eps=1e-5)
+DECAYING = dict(I=1024, N=50, seed=2011065303, eps=1e-5)
 
 
 def batched_subset() -> List[int]:
@@ -174,8 +174,9 @@ class OraclePool:
 
 
 def default_workers() -> int:
+    # leave cores to the test process, which draws the same inputs for the GPU meanwhile
     n = os.cpu_count() or 2
-    return max(1, min(16, n - 2))
+    return max(1, min(12, n - 4))
 
 
 _POOL = None

@@ -12,13 +12,15 @@ clause, with the tolerances of the mixed and batched forms).
   * the large-mode workload at full size: N=10, I_n=65536, formal ranks 32 (4.33 GB);
   * the paper's Model 1 (Sec. 4.2, Table 2): N=50, I_n=2000, Y = 2X - X with X of rank
     25 (formal ranks 50), in FP64 at eps=1e-8 and fp32x2 at eps=1e-6;
-  * the decaying-spectrum construction at N=50 (formal ranks 64, eps=1e-5) with I_n=2048,
+  * the decaying-spectrum construction at N=50 (formal ranks 64, eps=1e-5) with I_n=1024,
     in fp32x2 and FP64;
   * members 0..15, the largest and the smallest of the full-size 512-tensor batched
     recipe, rounded as one batch in fp32x2 and in FP64.
 
 The FP32-storage inputs are the FP32 roundings of the FP64 tensors the oracle rounds, so
-the reported error includes the input quantisation.
+the reported error includes the input quantisation.  Each test runs every precision of its
+workload on the GPU first and then submits all its error measurements to the pool at once,
+so that they run side by side.
 """
 import numpy as np
 import pytest
@@ -79,71 +81,82 @@ def test_large_modes_full_size_fp64(gpu, pool):
     assert err <= TOL64, err
 
 
-def model1_device(gpu, dtype):
+def test_paper_model1(gpu, pool):
     import torch
 
     X = oracle_pool.model1_x()
-    dX = gpu.from_host(X.I, X.R, X.cores, dtype=dtype)
-    two = gpu.DeviceTT(list(X.I), list(X.R), [2.0 * dX.cores[0]] + dX.cores[1:])
-    neg = gpu.DeviceTT(list(X.I), list(X.R), [-dX.cores[0]] + dX.cores[1:])
-    return gpu.tt_add(two, neg)
+    runs = []
+    for prec, eps, tol, dt in (("fp64", 1e-8, TOL64, torch.float64), ("fp32x2", 1e-6, TOL_MIXED, torch.float32)):
+        dX = gpu.from_host(X.I, X.R, X.cores, dtype=dt)
+        two = gpu.DeviceTT(list(X.I), list(X.R), [2.0 * dX.cores[0]] + dX.cores[1:])
+        neg = gpu.DeviceTT(list(X.I), list(X.R), [-dX.cores[0]] + dX.cores[1:])
+        Y = gpu.tt_add(two, neg)  # Y = 2X - X (Sec. 4.2), formal ranks 50
+        runs.append((prec, eps, tol, down(gpu.tt_round(Y, eps, precision=prec))))
+        del dX, two, neg, Y
+        release(gpu)
+    pending = []
+    for prec, eps, tol, got in runs:
+        ref = pool.get("model1_%g" % eps)
+        assert got.R == ref.R == ttgen.uniform_ranks(oracle_pool.MODEL1["N"], oracle_pool.MODEL1["r"]), (prec, got.R)
+        pending.append((prec, tol, pool.rel_err_async(got, ref)))
+    for prec, tol, p in pending:
+        err = p.get(1500)
+        assert err <= tol, (prec, err)
 
 
-@pytest.mark.parametrize("prec,eps,tol", [("fp64", 1e-8, TOL64), ("fp32x2", 1e-6, TOL_MIXED)])
-def test_paper_model1(gpu, pool, prec, eps, tol):
-    import torch
-
-    Y = model1_device(gpu, torch.float64 if prec == "fp64" else torch.float32)
-    got = down(gpu.tt_round(Y, eps, precision=prec))
-    del Y
-    release(gpu)
-    ref = pool.get("model1_%g" % eps)
-    r = oracle_pool.MODEL1["r"]
-    assert got.R == ref.R == ttgen.uniform_ranks(oracle_pool.MODEL1["N"], r), (got.R, ref.R)
-    err = pool.rel_err_async(got, ref).get(1500)
-    assert err <= tol, err
-
-
-@pytest.mark.parametrize("prec,tol", [("fp32x2", TOL_MIXED), ("fp64", TOL64)])
-def test_decaying_N50(gpu, pool, prec, tol):
+def test_decaying_N50(gpu, pool):
     terms = oracle_pool.decaying_terms()
     X = gpu.from_host(terms[0].I, terms[0].R, terms[0].cores)
     for T in terms[1:]:
         X = gpu.tt_add(X, gpu.from_host(T.I, T.R, T.cores))
     del terms
-    if prec != "fp64":
-        X = as32(gpu, X)
-    got = down(gpu.tt_round(X, oracle_pool.DECAYING["eps"], precision=prec))
+    runs = []
+    for prec, tol in (("fp32x2", TOL_MIXED), ("fp64", TOL64)):
+        x = X if prec == "fp64" else as32(gpu, X)
+        runs.append((prec, tol, down(gpu.tt_round(x, oracle_pool.DECAYING["eps"], precision=prec))))
+        del x
     del X
     release(gpu)
     ref = pool.get("decaying")
-    assert got.R == ref.R, (got.R, ref.R)
     assert max(ref.R) < 64  # the threshold cuts the decaying spectra (to ranks near 48)
-    err = pool.rel_err_async(got, ref).get(1500)
-    assert err <= tol, err
+    pending = []
+    for prec, tol, got in runs:
+        assert got.R == ref.R, (prec, got.R, ref.R)
+        pending.append((prec, tol, pool.rel_err_async(got, ref)))
+    for prec, tol, p in pending:
+        err = p.get(1500)
+        assert err <= tol, (prec, err)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32x2", TOL_MIXED), ("fp64", TOL64)])
-def test_batched_recipe_subset_full_size(gpu, pool, prec, tol):
+def test_batched_recipe_subset_full_size(gpu, pool):
     import torch
 
     members = oracle_pool.batched_subset()
     xs = []
     for t in members:
         (Y, Yp), _ = ttgen.batched_member(t)
-        X = gpu.tt_add(gpu.from_host(Y.I, Y.R, Y.cores), gpu.from_host(Yp.I, Yp.R, Yp.cores))
-        xs.append(X if prec == "fp64" else as32(gpu, X))
-        del Y, Yp, X
+        xs.append(gpu.tt_add(gpu.from_host(Y.I, Y.R, Y.cores), gpu.from_host(Yp.I, Yp.R, Yp.cores)))
+        del Y, Yp
     torch.cuda.synchronize()
-    outs = gpu.tt_round_batched(xs, [1e-6] * len(xs), precision=prec)
-    gots = [down(o) for o in outs]
-    del xs, outs
+    gots = {}
+    for prec in ("fp32x2", "fp64"):
+        batch = xs if prec == "fp64" else [as32(gpu, x) for x in xs]
+        outs = gpu.tt_round_batched(batch, [1e-6] * len(batch), precision=prec)
+        gots[prec] = [down(o) for o in outs]
+        del batch, outs
+        release(gpu)
+    del xs
     release(gpu)
     pending = []
-    for t, got in zip(members, gots):
+    for i, t in enumerate(members):
         ref = pool.get("batched_%d" % t)
-        assert got.R == ref.R, (t, got.R, ref.R)
-        pending.append((t, pool.rel_err_async(got, ref)))
-    errs = {t: p.get(1500) for t, p in pending}
-    bad = {t: e for t, e in errs.items() if not e <= tol}
+        for prec, tol in (("fp32x2", TOL_MIXED), ("fp64", TOL64)):
+            got = gots[prec][i]
+            assert got.R == ref.R, (t, prec, got.R, ref.R)
+            pending.append((t, prec, tol, pool.rel_err_async(got, ref)))
+    bad = {}
+    for t, prec, tol, p in pending:
+        e = p.get(1500)
+        if not e <= tol:
+            bad[(t, prec)] = e
     assert not bad, bad
