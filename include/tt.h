@@ -57,8 +57,8 @@ typedef enum {
   TT_ERR_WORKSPACE = 2,   /* workspace missing or smaller than the size query returned */
   TT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   TT_ERR_NUMERICAL = 4,   /* non-finite values met, or an SVD did not converge */
-  TT_ERR_UNSUPPORTED = 6  /* a rank whose buffers the planner cannot place (above 117
-                             for 3-D cores; every rank above TT_MAX_RANK) */
+  TT_ERR_UNSUPPORTED = 6  /* a rank above TT_MAX_RANK, or a shape whose buffers the
+                             planner cannot place */
 } tt_status;
 
 typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
@@ -71,7 +71,7 @@ typedef enum {
 } tt_precision;
 
 /* Largest rank (R[n]) any routine accepts. */
-#define TT_MAX_RANK 128
+#define TT_MAX_RANK 160
 
 typedef struct {
   int32_t N;            /* number of cores, >= 1 */

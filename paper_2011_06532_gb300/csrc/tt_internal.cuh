@@ -319,6 +319,210 @@ __device__ __forceinline__ int tile_rows_for(int j, int M, int tri_off, int q = 
   return tri_off < 0 ? M : min(M, max(0, (j - tri_off + 1) * q));
 }
 
+// Reflector-by-reflector forms, used for the FP32-storage compute types (df32, float), whose
+// serial chains are short on the wide FP32 pipes.
+template <typename T>
+__device__ int hh_factor_seq(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+                         int tri_off = -1, int q = 1) {
+  const int kk = min(k + M, b);
+  // Narrow factors: warp 0 forms reflector j (column norm, square root, reciprocal) while
+  // the other warps apply the scaling still owed by the stored column of reflector pj
+  // (rows pr0..pM-1); then the whole CTA applies reflector j.
+  int pj = -1, pr0 = 0, pM = 0;
+  T pend = T(1);
+  for (int j = 0; j < kk; ++j) {
+    const int r0 = j < k ? 0 : j - k + 1;
+    const int Mj = tile_rows_for(j, M, tri_off, q);
+    T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
+    if (threadIdx.x >= 32 && pj >= 0) {
+      for (int r = pr0 + (int)threadIdx.x - 32; r < pM; r += NT - 32) tile[(size_t)r * ldt + pj] *= pend;
+    }
+    if (threadIdx.x < 32) {
+      T ss = T(0);
+      for (int r = r0 + threadIdx.x; r < Mj; r += 32) {
+        const T v = tile[(size_t)r * ldt + j];
+        ss += v * v;
+      }
+      ss = warp_sum(ss);
+      if (threadIdx.x == 0) {
+        T tj = T(0), scale = T(0);
+        if (ss != T(0)) {
+          const T alpha = piv[j];
+          const T v = alpha * alpha + ss;
+          const bool fast = std::is_same<T, double>::value && nr_range((double)v);
+          const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
+          const T beta = alpha >= T(0) ? -nrm : nrm;
+          const T d = alpha - beta;
+          const T bd = beta * d;
+          if (fast && nr_range(fabs((double)bd))) {
+            // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q
+            // and 1 / d = beta q
+            const T q = (T)rcp_nr((double)bd);
+            tj = -d * d * q;
+            scale = beta * q;
+          } else {
+            // textbook form; tau lies in [1, 2] whatever the scale of the column
+            tj = (beta - alpha) / beta;
+            scale = T(1) / d;
+          }
+          piv[j] = beta;
+        }
+        tau[j] = tj;
+        s.sc[0] = scale;
+        s.sc[1] = tj;
+      }
+    }
+    __syncthreads();
+    const T tj = s.sc[1];
+    pj = -1;
+    if (tj != T(0)) {
+      const T scale = s.sc[0];
+      reflect(tj, tile + j, ldt, r0, Mj, piv + j + 1, tile + j + 1, ldt, b - j - 1, s, scale);
+      pj = j;
+      pend = scale;
+      pr0 = r0;
+      pM = Mj;
+    } else {
+      __syncthreads();
+    }
+  }
+  if (pj >= 0) {
+    for (int r = pr0 + (int)threadIdx.x; r < pM; r += NT) tile[(size_t)r * ldt + pj] *= pend;
+  }
+  __syncthreads();
+  return kk;
+}
+
+template <typename T>
+__device__ int hh_factor_ahead(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
+                         int tri_off = -1, int q = 1) {
+  const int kk = min(k + M, b);
+  const int t = threadIdx.x;
+  // Wide factors: warp 0 forms reflector j (column norm, then the square root / reciprocal
+  // chain) while the other warps apply the scaling still owed by the stored column of
+  // reflector pj (rows pr0..pM-1) and already take the dot products of reflector j's
+  // unscaled column with the trailing columns (the scalars are needed only when w is
+  // formed).
+  const int nth = NT - 32;
+  int pj = -1, pr0 = 0, pM = 0;
+  T pend = T(1);
+  auto dots = [&](int u, int j, int r0, int Mj, int nc, int G) {
+    if (nc > 0 && u < G * nc) {
+      const int g = u / nc, c = u - g * nc;
+      const T *X = tile + j + 1 + c;
+      if constexpr (is_df<T>::value) {
+        float sh = 0.f, sl = 0.f;
+        for (int r = r0 + g; r < Mj; r += G) df_dot_acc(sh, sl, tile[(size_t)r * ldt + j], X[(size_t)r * ldt]);
+        s.red[g * nc + c] = df_finish(sh, sl);
+      } else {
+        T acc = T(0);
+        for (int r = r0 + g; r < Mj; r += G) acc += tile[(size_t)r * ldt + j] * X[(size_t)r * ldt];
+        s.red[g * nc + c] = acc;
+      }
+    }
+  };
+  for (int j = 0; j < kk; ++j) {
+    const int r0 = j < k ? 0 : j - k + 1;
+    const int Mj = tile_rows_for(j, M, tri_off, q);
+    T *piv = j < k ? Rr + (size_t)j * ldr : tile + (size_t)(j - k) * ldt;
+    const int nc = b - j - 1, nrow = Mj - r0;
+    // dot-product groups over the nth threads taking them (nc < b <= TT_MAX_RANK < NT - 32)
+    int G = nc > 0 ? nth / nc : 1;
+    if (G > nrow) G = nrow > 0 ? nrow : 1;
+    if (t < 32) {
+      T ss = T(0);
+      for (int r = r0 + t; r < Mj; r += 32) {
+        const T v = tile[(size_t)r * ldt + j];
+        ss += v * v;
+      }
+      ss = warp_sum(ss);
+      if (t == 0) {
+        T tj = T(0), scale = T(0);
+        if (ss != T(0)) {
+          const T alpha = piv[j];
+          const T v = alpha * alpha + ss;
+          const bool fast = std::is_same<T, double>::value && nr_range((double)v);
+          const T nrm = fast ? (T)((double)v * rsqrt_nr((double)v)) : tsqrt(v);
+          const T beta = alpha >= T(0) ? -nrm : nrm;
+          const T d = alpha - beta;
+          const T bd = beta * d;
+          if (fast && nr_range(fabs((double)bd))) {
+            // one reciprocal: with q = 1 / (beta d), tau = (beta - alpha) / beta = -d d q
+            // and 1 / d = beta q
+            const T qq = (T)rcp_nr((double)bd);
+            tj = -d * d * qq;
+            scale = beta * qq;
+          } else {
+            // textbook form; tau lies in [1, 2] whatever the scale of the column
+            tj = (beta - alpha) / beta;
+            scale = T(1) / d;
+          }
+          piv[j] = beta;
+        }
+        tau[j] = tj;
+        s.sc[0] = scale;
+        s.sc[1] = tj;
+      }
+    } else {
+      const int u = t - 32;
+      if (pj >= 0)
+        for (int r = pr0 + u; r < pM; r += NT - 32) tile[(size_t)r * ldt + pj] *= pend;
+      dots(u, j, r0, Mj, nc, G);
+    }
+    __syncthreads();
+    const T tj = s.sc[1];
+    pj = -1;
+    if (tj != T(0)) {
+      const T scale = s.sc[0];
+      if (nc > 0) {
+        for (int h = G; h > 1;) {
+          const int half = (h + 1) >> 1;
+          for (int idx = t; idx < (h - half) * nc; idx += NT) s.red[idx] += s.red[idx + half * nc];
+          h = half;
+          __syncthreads();
+        }
+        T *p = piv + j + 1;
+        if (t < nc) {
+          const T w = tj * (p[t] + scale * s.red[t]);
+          s.wbuf[t] = scale * w;
+          p[t] -= w;
+        }
+        __syncthreads();
+        if (nrow > 0) {
+          // dense walk over the nrow x nc trailing block: X -= v w^T (v unscaled, w scaled)
+          const int dq = NT / nc, dr = NT - dq * nc;
+          int r = t / nc, cc = t - (t / nc) * nc;
+          for (; r < nrow;) {
+            const size_t rr = (size_t)(r0 + r);
+            if constexpr (is_df<T>::value) {
+              T &x = tile[rr * ldt + j + 1 + cc];
+              x = df_sub_prod(x, tile[rr * ldt + j], s.wbuf[cc]);
+            } else {
+              tile[rr * ldt + j + 1 + cc] -= tile[rr * ldt + j] * s.wbuf[cc];
+            }
+            r += dq;
+            cc += dr;
+            if (cc >= nc) {
+              cc -= nc;
+              ++r;
+            }
+          }
+        }
+      }
+      pj = j;
+      pend = scale;
+      pr0 = r0;
+      pM = Mj;
+    }
+    __syncthreads();
+  }
+  if (pj >= 0) {
+    for (int r = pr0 + t; r < pM; r += NT) tile[(size_t)r * ldt + pj] *= pend;
+  }
+  __syncthreads();
+  return kk;
+}
+
 // Named CTA barriers (PTX bar.sync / bar.arrive with an id and a thread count; id 0 is
 // __syncthreads).  bar.arrive lets a warp signal a barrier without waiting at it.
 __device__ __forceinline__ void nbar_sync(int id, int count) {
@@ -506,10 +710,23 @@ __device__ int hh_factor_la(T *Rr, int ldr, int k, T *tile, int ldt, int M, int 
 }
 
 // Householder QR of the stacked matrix (see above): the look-ahead form.
+// FP64 takes the look-ahead form: each FP64 instruction of the scalar chain holds an SMSP's
+// FP64 unit ~64 cycles, so the chain must run beside the bulk work.  The FP32-storage types
+// (df32, float) keep the reflector-by-reflector forms: their chains are short on the FP32
+// pipes, and a single warp updating the next column and forming its reflector in double-float
+// arithmetic measured slower than all warps sharing that column (N=50, I_n=16384, rank 64:
+// fp32x2 2.20 s reflector by reflector, 2.50 s look-ahead).  Factors of 48 or more columns
+// take reflector j's dot products while its scalars are being formed (hh_factor_ahead);
+// narrower ones measured faster with all threads on the dot products after the scalars.
 template <typename T>
 __device__ int hh_factor(T *Rr, int ldr, int k, T *tile, int ldt, int M, int b, T *tau, Scratch<T> s,
                          int tri_off = -1, int q = 1) {
-  return hh_factor_la(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q);
+  if constexpr (std::is_same<T, double>::value) {
+    return hh_factor_la(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q);
+  } else {
+    return b >= 48 ? hh_factor_ahead(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q)
+                   : hh_factor_seq(Rr, ldr, k, tile, ldt, M, b, tau, s, tri_off, q);
+  }
 }
 
 // Moves the new R rows k..kk-1 produced by hh_factor from the tile into Rr (zeroing the
@@ -560,8 +777,12 @@ __device__ __host__ __forceinline__ int apply_group(int nc) {
   const int g = nc > 0 ? NT / nc : 4;
   return g >= 4 ? 4 : (g < 1 ? 1 : g);
 }
-// entries of the per-tile T storage (upper triangles of the groups' T), for b reflectors
-__device__ __host__ __forceinline__ int apply_tstore(int b) { return ((b + 1) / 2) * 10 + 10; }
+// entries of the per-tile T storage (packed upper triangles of 10 entries, one per group) for
+// b reflectors applied to blocks of at most nc columns
+__device__ __host__ __forceinline__ int apply_tstore(int b, int nc) {
+  const int g = apply_group(nc);
+  return ((b + g - 1) / g) * 10 + 10;
+}
 
 template <typename T>
 __device__ __forceinline__ T refl_entry(const T *V, int ldv, int k, int j, int r) {
@@ -574,10 +795,16 @@ __device__ __forceinline__ T refl_entry(const T *V, int ldv, int k, int j, int r
 __device__ __forceinline__ int tri_idx(int a, int b) { return a + (b * (b + 1)) / 2; }
 
 // Q_t [CR; CT] for the reflectors of one hh_factor step on a dense tile (see hh_apply);
-// Tst: shared scratch of apply_tstore(b) elements; s.wbuf must hold NT elements.
+// Tst: scratch of apply_tstore(b, nc) elements; s.wbuf must hold NT elements.
 template <typename T>
 __device__ void hh_apply_grouped(const T *V, int ldv, const T *tau, int k, int M, int b, T *CR, int ldcr, T *CT,
                                  int ldct, int nc, Scratch<T> s, T *Tst) {
+  if constexpr (!std::is_same<T, double>::value) {
+    // FP32-storage types: reflector by reflector (their reductions are cheap on the FP32
+    // pipes; the grouped form measured slower there)
+    hh_apply(V, ldv, tau, k, M, b, CR, ldcr, CT, ldct, nc, s);
+    return;
+  }
   const int kk = min(k + M, b);
   if (kk <= 0 || nc <= 0) return;
   const int t = threadIdx.x;

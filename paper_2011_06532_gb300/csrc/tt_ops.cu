@@ -131,17 +131,24 @@ constexpr int kDotBlocks = 304;  // CTAs per core (2 per SM); partial sums are r
 template <typename T>
 __global__ void __launch_bounds__(256) k_dot_core(const T *__restrict__ X, const T *__restrict__ Y, int64_t I, int rx0,
                                                   int rx1, int ry0, int ry1, const double *__restrict__ W,
-                                                  double *__restrict__ partial, int *E) {
+                                                  double *__restrict__ partial, int *E, int big) {
+  // big = 0: W (scaled), Z and the accumulator in shared memory; big = 1 (ranks whose three
+  // blocks do not fit): only Z in shared memory, W read from global memory and scaled on the
+  // fly, the accumulator kept in this block's slice of `partial` (no other block touches it)
   extern __shared__ __align__(16) unsigned char smem[];
   T *Ws = reinterpret_cast<T *>(smem);
-  T *Zs = Ws + ry0 * rx0;
-  double *acc = reinterpret_cast<double *>(smem + ((sizeof(T) * (size_t)(ry0 * rx0 + ry0 * rx1) + 15) / 16) * 16);
+  T *Zs = big ? reinterpret_cast<T *>(smem) : Ws + ry0 * rx0;
+  double *out = partial + (size_t)blockIdx.x * ry1 * rx1;
+  double *acc = big ? out
+                    : reinterpret_cast<double *>(smem + ((sizeof(T) * (size_t)(ry0 * rx0 + ry0 * rx1) + 15) / 16) * 16);
   __shared__ double red[8];
   const int t = threadIdx.x;
   // W_{n-1} enters in [2^-32, 2^32] up to an exact power of two, accumulated in E (every
   // block finds the same exponent; block 0 records it)
   const int e = range_exp(block_absmax(W, ry0 * rx0, red));
-  for (int idx = t; idx < ry0 * rx0; idx += blockDim.x) Ws[idx] = (T)ldexp(W[idx], -e);
+  const double wsc = ldexp(1.0, -e);
+  if (!big)
+    for (int idx = t; idx < ry0 * rx0; idx += blockDim.x) Ws[idx] = (T)ldexp(W[idx], -e);
   if (blockIdx.x == 0 && t == 0 && e != 0) *E += e;
   for (int idx = t; idx < ry1 * rx1; idx += blockDim.x) acc[idx] = 0.0;
   __syncthreads();
@@ -152,7 +159,11 @@ __global__ void __launch_bounds__(256) k_dot_core(const T *__restrict__ X, const
       const int p = idx / rx1, s = idx - p * rx1;
       T z = T(0);
       const T *xc = X + (int64_t)rx0 * (i + I * s);
-      for (int r = 0; r < rx0; ++r) z += Ws[p * rx0 + r] * xc[r];
+      if (big) {
+        for (int r = 0; r < rx0; ++r) z += (T)(W[p * rx0 + r] * wsc) * xc[r];
+      } else {
+        for (int r = 0; r < rx0; ++r) z += Ws[p * rx0 + r] * xc[r];
+      }
       Zs[idx] = z;
     }
     __syncthreads();
@@ -166,8 +177,8 @@ __global__ void __launch_bounds__(256) k_dot_core(const T *__restrict__ X, const
     }
     __syncthreads();
   }
-  double *out = partial + (size_t)blockIdx.x * ry1 * rx1;
-  for (int idx = t; idx < ry1 * rx1; idx += blockDim.x) out[idx] = acc[idx];
+  if (!big)
+    for (int idx = t; idx < ry1 * rx1; idx += blockDim.x) out[idx] = acc[idx];
 }
 
 __global__ void k_dot_reduce(const double *__restrict__ partial, int nblk, int n, double *__restrict__ W) {
@@ -219,19 +230,21 @@ int dot_run(const tt_tensor *a, const tt_tensor *b, double *result, void *ws, si
     const int rx0 = (int)a->R[n], rx1 = (int)a->R[n + 1], ry0 = (int)b->R[n], ry1 = (int)b->R[n + 1];
     const int nb = dot_blocks(a->I[n]);
     const size_t es = a->dtype == TT_F64 ? 8 : 4;
-    const size_t smem = ((es * (size_t)(ry0 * rx0 + ry0 * rx1) + 15) / 16) * 16 + sizeof(double) * ry1 * rx1;
+    size_t smem = ((es * (size_t)(ry0 * rx0 + ry0 * rx1) + 15) / 16) * 16 + sizeof(double) * ry1 * rx1;
+    const int big = smem > 220 * 1024 ? 1 : 0;
+    if (big) smem = es * (size_t)ry0 * rx1;
     if (smem > 220 * 1024) return TT_ERR_UNSUPPORTED;
     TraceScope ts_(TT_K_DOT, st);
     if (a->dtype == TT_F64) {
       if (smem > 48 * 1024)
         TT_CUDA(cudaFuncSetAttribute(k_dot_core<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_dot_core<double><<<nb, 256, smem, st>>>((const double *)a->cores[n], (const double *)b->cores[n], a->I[n],
-                                                  rx0, rx1, ry0, ry1, W0, part, E);
+                                                  rx0, rx1, ry0, ry1, W0, part, E, big);
     } else {
       if (smem > 48 * 1024)
         TT_CUDA(cudaFuncSetAttribute(k_dot_core<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
       k_dot_core<float><<<nb, 256, smem, st>>>((const float *)a->cores[n], (const float *)b->cores[n], a->I[n], rx0,
-                                                 rx1, ry0, ry1, W0, part, E);
+                                                 rx1, ry0, ry1, W0, part, E, big);
     }
     TT_CUDA(cudaGetLastError());
     {

@@ -169,6 +169,8 @@ struct SvdArgs {
   int ldu;
   int *status;
   int precond;          // run the FP32 pre-sweeps (shared memory permitting)
+  double *Vg;           // K x K rotation accumulator in global memory when the shared memory
+                        // holds only A (ranks above ~117), else nullptr
 };
 
 // ------------------------------------------------------------------------------------
@@ -245,8 +247,12 @@ __global__ void __launch_bounds__(NT) k_s1_leaf(S1Args<S, T> a) {
         const int chunk = nt * b;
         for (int idx = t; idx < cc_n * chunk; idx += NT) {
           const int cc = idx / chunk, rem = idx - cc * chunk;
-          const int il = rem / b;
-          Xs[idx] = src_load<T>(a.X, rem - il * b, i0 + il, c0 + cc);
+          if (!a.X.B) {
+            Xs[idx] = T(a.X.X[(size_t)b * (i0 + (int64_t)a.g.I * (c0 + cc)) + rem]);
+          } else {
+            const int il = rem / b;
+            Xs[idx] = src_load<T>(a.X, rem - il * b, i0 + il, c0 + cc);
+          }
         }
         __syncthreads();
         // one copy of the loop per place the factor is read from (FP64 global, staged
@@ -520,7 +526,7 @@ __device__ __forceinline__ S out_scale(const int *E, int n, int N) {
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *Q = sm<T>(smem, a.oQ), *CT = sm<T>(smem, a.oCT);
+  T *Q = sm<T>(smem, a.oQ), *CT = buf<T>(smem, a.oCT, a.gscr, a.gstride);
   T *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride), *Rr = buf<T>(smem, a.oRr, a.gscr, a.gstride);
   T *Xs = sm<T>(smem, a.oXs), *Ps = buf<T>(smem, a.oPs, a.gscr, a.gstride);
   Scratch<T> s{sm<T>(smem, a.oRed), buf<T>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
@@ -631,7 +637,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
 template <typename S, typename T>
 __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *V = sm<T>(smem, a.oV), *CT = sm<T>(smem, a.oCT), *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride);
+  T *V = sm<T>(smem, a.oV), *CT = buf<T>(smem, a.oCT, a.gscr, a.gstride), *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride);
   Scratch<T> s{sm<T>(smem, a.oRed), buf<T>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
   T *tv = sm<T>(smem, a.oTau);
   const int p = blockIdx.x, t = threadIdx.x;
@@ -745,7 +751,7 @@ __device__ __forceinline__ T seg_sum(T v) {
 // pos holds 2 * (ns + 2) ints, flag 2 ints.
 template <typename T>
 __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2,
-                       bool quad_stop = false) {
+                       bool quad_stop = false, bool accumulate_v = true) {
   constexpr int LP = 8, PW = 32 / LP;  // lanes per pair, pairs per warp
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   const int seg = lane / LP, sl = lane - seg * LP;
@@ -797,11 +803,13 @@ __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, i
           bp[r] = cs * x - sn * y;
           bq[r] = sn * x + cs * y;
         }
-        T *vp = V + (size_t)pp * ns, *vq = V + (size_t)qq * ns;
-        for (int r = sl; r < ns; r += LP) {
-          const T x = vp[r], y = vq[r];
-          vp[r] = cs * x - sn * y;
-          vq[r] = sn * x + cs * y;
+        if (accumulate_v) {
+          T *vp = V + (size_t)pp * ns, *vq = V + (size_t)qq * ns;
+          for (int r = sl; r < ns; r += LP) {
+            const T x = vp[r], y = vq[r];
+            vp[r] = cs * x - sn * y;
+            vq[r] = sn * x + cs * y;
+          }
         }
         if (sl == 0) flag[0] = 1;
       }
@@ -834,8 +842,8 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   const bool wide = kroot < K;
   const int ms = K, ns = wide ? kroot : K;  // A is ms x ns, column-major, ms >= ns
   double *A = reinterpret_cast<double *>(smem);
-  double *Vm = A + (size_t)ms * ns;
-  double *W = Vm + (size_t)ns * ns;
+  double *Vm = a.Vg ? a.Vg : A + (size_t)ms * ns;
+  double *W = a.Vg ? A + (size_t)ms * ns : Vm + (size_t)ns * ns;
   const bool pre = a.precond != 0;
   double *sig = pre ? W + svd_w_doubles(ms, ns) : W;
   int *pos = reinterpret_cast<int *>(sig + ns);  // 2 * (ns + 2)
@@ -946,7 +954,9 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   }
   const double neg2 = sig[0];
   __syncthreads();
-  const bool converged = jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, true);
+  // A square root factor (not wide) needs no rotation accumulator: the next core's factor
+  // V Sigma equals R^T U (R = U Sigma V^T) and is formed from R and U_hat below.
+  const bool converged = jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, true, wide);
   // singular values
   const int lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   for (int c = warp; c < ns; c += nwarp) {
@@ -1000,13 +1010,24 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
     const int c = ord[l];
     const double sg = sig[c];
     if (!wide) {
-      // R' = U S V^T : U_hat = A(:, c) / sigma, C_next = V(:, c) sigma
+      // R' = U S V^T : U_hat = A(:, c) / sigma (C_next = R'^T U_hat below)
       a.Uhat[(size_t)r * a.ldu + l] = sg > 0.0 ? A[(size_t)c * ms + r] / sg : (r == l ? 1.0 : 0.0);
-      a.Cnext[(size_t)r * a.ldu + l] = Vm[(size_t)c * ns + r] * sg;
     } else {
       // R'^T = U' S V'^T : U_hat = V'(:, c) (kroot rows), C_next = A(:, c) (= U' sigma)
       if (r < kroot) a.Uhat[(size_t)r * a.ldu + l] = Vm[(size_t)c * ns + r];
       a.Cnext[(size_t)r * a.ldu + l] = A[(size_t)c * ms + r];
+    }
+  }
+  if (!wide) {
+    // C_next(:, l) = V(:, c) sigma_c = R'^T U_hat(:, l) (zero for sigma_c = 0, whose U_hat
+    // column is a unit vector, not a singular vector)
+    __syncthreads();
+    for (int idx = t; idx < K * L; idx += SVD_NT) {
+      const int r = idx / L, l = idx - r * L;
+      double acc = 0.0;
+      if (sig[ord[l]] > 0.0)
+        for (int i = 0; i < K; ++i) acc += a.Rroot[(size_t)i * K + r] * a.Uhat[(size_t)i * a.ldu + l];
+      a.Cnext[(size_t)r * a.ldu + l] = acc;
     }
   }
 }
@@ -1172,10 +1193,11 @@ int leaves_for(int64_t I, int64_t rows, int b, int nsm) {
 // at the next free element of the per-leaf global scratch (negative encoded offset)
 struct Place {
   Carve c;
-  bool spill;
+  int spill;  // 0: all in shared memory; 1: running factors and carried blocks to the global
+              // scratch; 2: also the carried tile block CT (ranks above ~120)
   size_t g = 0;
-  int take(size_t bytes, size_t elems, bool spillable) {
-    if (spill && spillable) {
+  int take(size_t bytes, size_t elems, int level) {
+    if (level > 0 && spill >= level) {
       const int off = -1 - (int)g;
       g += elems;
       return off;
@@ -1191,21 +1213,21 @@ struct SmemS1 {
 };
 
 template <typename T>
-SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, bool spill = false, bool stage_p = false) {
+SmemS1<T> smem_s1(int b, int rho, int cin, int Tt, int CC, int spill = 0, bool stage_p = false) {
   SmemS1<T> m;
   Place pl{Carve(), spill};
   Carve &c = pl.c;
   m.ldt = b + 1;
-  m.oRr = pl.take(sizeof(T) * b * b, (size_t)b * b, true);
+  m.oRr = pl.take(sizeof(T) * b * b, (size_t)b * b, 1);
   m.oTile = (int)c.take(sizeof(T) * (size_t)Tt * rho * m.ldt);
   m.oXs = (int)c.take(sizeof(T) * (size_t)CC * Tt * b);
   // the pushed factor's staged copy (FP32-storage types only, see k_s1_leaf)
   m.oPs = stage_p && !std::is_same<T, double>::value
-              ? pl.take(sizeof(T) * (size_t)rho * cin, (size_t)rho * cin, true)
+              ? pl.take(sizeof(T) * (size_t)rho * cin, (size_t)rho * cin, 1)
               : (int)c.take(16);
   m.oRed = (int)c.take(sizeof(T) * NT);
   m.oW = (int)c.take(sizeof(T) * std::max(b, 1));
-  m.oSc = (int)c.take(sizeof(T) * 4);  // reflector scalars, double-buffered (hh_factor_la)
+  m.oSc = (int)c.take(sizeof(T) * (std::is_same<T, double>::value ? 4 : 2));  // reflector scalars
   m.oTau = (int)c.take(sizeof(T) * b);
   m.bytes = c.off;
   m.gstride = pl.g;
@@ -1220,7 +1242,7 @@ struct SmemS2 {
 
 // mode A/last: b1 = R_n, K1 = K_{n+1}, Lmax = max rows per slice of V(Y_n) (<= K_n)
 template <typename T>
-SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC, bool spill = false) {
+SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC, int spill = 0) {
   SmemS2<T> m;
   Place pl{Carve(), spill};
   Carve &c = pl.c;
@@ -1230,18 +1252,21 @@ SmemS2<T> smem_s2(int mode, int b1, int K1, int Lmax, int Tt, int cin, int CC, b
   size_t vrows = (size_t)Tt * (mode == 1 ? 1 : Lmax);
   size_t qbytes = std::max(qrows * m.ldq, mode == 2 ? 0 : vrows * m.ldv) * sizeof(T);
   m.oQ = (int)c.take(qbytes);
-  m.oCT = (int)c.take(sizeof(T) * (mode == 1 ? 1 : qrows * Lmax));
-  m.oCR = pl.take(sizeof(T) * (mode == 1 ? 1 : (size_t)b1 * Lmax), mode == 1 ? 1 : (size_t)b1 * Lmax, true);
-  m.oRr = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, true);
+  m.oCT = pl.take(sizeof(T) * (mode == 1 ? 1 : qrows * Lmax), mode == 1 ? 1 : qrows * Lmax, 2);
+  m.oCR = pl.take(sizeof(T) * (mode == 1 ? 1 : (size_t)b1 * Lmax), mode == 1 ? 1 : (size_t)b1 * Lmax, 1);
+  m.oRr = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, 1);
   m.oXs = (int)c.take(sizeof(T) * (mode == 1 ? (size_t)CC * Tt : 1));
-  m.oPs = pl.take(sizeof(T) * (mode == 1 ? (size_t)K1 * cin : 1), mode == 1 ? (size_t)K1 * cin : 1, true);
+  m.oPs = pl.take(sizeof(T) * (mode == 1 ? (size_t)K1 * cin : 1), mode == 1 ? (size_t)K1 * cin : 1, 1);
   m.oRed = (int)c.take(sizeof(T) * NT);
   // the grouped apply's W and T store go to the per-leaf global scratch with the other
   // spilled buffers when a core's buffers do not fit in shared memory
-  const size_t nw = (size_t)std::max(std::max(std::max(b1, K1), Lmax), NT);
-  m.oW = pl.take(sizeof(T) * nw, nw, true);
-  m.oTs = pl.take(sizeof(T) * apply_tstore(std::max(b1, 1)), (size_t)apply_tstore(std::max(b1, 1)), true);
-  m.oSc = (int)c.take(sizeof(T) * 4);  // reflector scalars, double-buffered (hh_factor_la)
+  // (FP64 only: the FP32-storage types apply reflector by reflector, see hh_apply_grouped)
+  constexpr bool grouped = std::is_same<T, double>::value;
+  const size_t nw = (size_t)std::max(std::max(std::max(b1, K1), Lmax), grouped ? NT : 1);
+  m.oW = pl.take(sizeof(T) * nw, nw, 1);
+  const int nts = grouped ? apply_tstore(std::max(b1, 1), std::max(Lmax, 1)) : 1;
+  m.oTs = pl.take(sizeof(T) * nts, (size_t)nts, 1);
+  m.oSc = (int)c.take(sizeof(T) * (grouped ? 4 : 2));  // reflector scalars (double-buffered in hh_factor_la)
   m.oTq = (int)c.take(sizeof(T) * std::max(b1, 1));
   m.oTv = (int)c.take(sizeof(T) * K1);
   m.bytes = c.off;
@@ -1256,19 +1281,21 @@ struct SmemOut {
 };
 
 template <typename T>
-SmemOut<T> smem_out(int K1, int Lmax, int Tt, bool spill = false) {
+SmemOut<T> smem_out(int K1, int Lmax, int Tt, int spill = 0) {
   SmemOut<T> m;
   Place pl{Carve(), spill};
   Carve &c = pl.c;
   m.ldv = K1 + 1;
   m.oV = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * m.ldv);
-  m.oCT = (int)c.take(sizeof(T) * (size_t)Tt * Lmax * K1);
-  m.oCR = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, true);
+  m.oCT = pl.take(sizeof(T) * (size_t)Tt * Lmax * K1, (size_t)Tt * Lmax * K1, 2);
+  m.oCR = pl.take(sizeof(T) * (size_t)K1 * K1, (size_t)K1 * K1, 1);
   m.oRed = (int)c.take(sizeof(T) * NT);
-  const size_t nw = (size_t)std::max(K1, NT);
-  m.oW = pl.take(sizeof(T) * nw, nw, true);
-  m.oTs = pl.take(sizeof(T) * apply_tstore(std::max(K1, 1)), (size_t)apply_tstore(std::max(K1, 1)), true);
-  m.oSc = (int)c.take(sizeof(T) * 4);  // reflector scalars, double-buffered (hh_factor_la)
+  constexpr bool grouped = std::is_same<T, double>::value;  // see smem_s2
+  const size_t nw = (size_t)std::max(K1, grouped ? NT : 1);
+  m.oW = pl.take(sizeof(T) * nw, nw, 1);
+  const int nts = grouped ? apply_tstore(std::max(K1, 1), std::max(K1, 1)) : 1;  // Ln <= K1 columns
+  m.oTs = pl.take(sizeof(T) * nts, (size_t)nts, 1);
+  m.oSc = (int)c.take(sizeof(T) * (grouped ? 4 : 2));
   m.oTau = (int)c.take(sizeof(T) * K1);
   m.bytes = c.off;
   m.gstride = pl.g;
@@ -1345,10 +1372,12 @@ int tree_fanin(int b) {
   return 2;
 }
 
-// shared bytes of k_svd for K columns (ms = ns = K is the largest case)
-size_t smem_svd(int K, bool precond) {
+// shared bytes of k_svd for K columns (ms = ns = K is the largest case); vglobal: the
+// rotation accumulator V lives in global memory
+size_t smem_svd(int K, bool precond, bool vglobal = false) {
   const size_t w = precond ? svd_w_doubles(K, K) : 0;
-  return sizeof(double) * ((size_t)K * K * 2 + w + K + SVD_NT / 32 + 1) + sizeof(int) * (3 * (size_t)K + 16);
+  return sizeof(double) * ((size_t)K * K * (vglobal ? 1 : 2) + w + K + SVD_NT / 32 + 1) +
+         sizeof(int) * (3 * (size_t)K + 16);
 }
 
 struct CorePlan {
@@ -1357,7 +1386,7 @@ struct CorePlan {
   int K0 = 1, K1 = 1;  // ranks after sweep 1
   int P = 1, Tt = 1;
   int Tt_want = 0;     // tuned tile (0 = heuristic); clamped to what fits
-  bool spill = false;  // running factor / carried block in global scratch
+  int spill = 0;  // 1: running factor / carried blocks in global scratch, 2: also the tile block CT
   Tree tree;
   size_t refl_off = 0, tau_off = 0, slot_off = 0;  // sweep-1 storage (n >= 1)
 };
@@ -1387,7 +1416,7 @@ struct RoundPlan {
   std::vector<CorePlan> core;
   // workspace layout (bytes)
   size_t off_ctl = 0, off_L = 0, off_scal = 0, off_status = 0, off_P = 0, off_P32 = 0;
-  size_t off_R = 0, off_C1 = 0, off_C2 = 0, off_slots2 = 0, off_refl2 = 0, off_tau2 = 0, off_part = 0;
+  size_t off_R = 0, off_C1 = 0, off_C2 = 0, off_slots2 = 0, off_refl2 = 0, off_tau2 = 0, off_part = 0, off_svdV = 0;
   size_t max_nodes = 0, max_slots = 0;
   size_t total = 0;
   int tree_MT[TT_MAX_RANK + 1];
@@ -1402,7 +1431,7 @@ int device_sm_count() {
 
 // largest shared-memory footprint of the kernels that core n runs with tile Tt
 template <typename T>
-static size_t core_smem(const RoundPlan &pl, int n, int Tt, bool spill, bool sweep1_only, size_t *gstride) {
+static size_t core_smem(const RoundPlan &pl, int n, int Tt, int spill, bool sweep1_only, size_t *gstride) {
   const CorePlan &c = pl.core[n];
   const int N = pl.N, CC = 8;
   size_t mx = 0, g = 0;
@@ -1447,8 +1476,8 @@ static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
     const int64_t per_leaf = (c.I + c.P - 1) / c.P;
     const int maxT = n == 0 ? 512 : 64;
     int best = 0;
-    for (int sp = 0; sp < 2 && best == 0; ++sp) {
-      c.spill = sp == 1;
+    for (int sp = 0; sp < 3 && best == 0; ++sp) {
+      c.spill = sp;
       for (int Tt = 1; Tt <= maxT && Tt <= per_leaf; ++Tt) {
         if (n >= 1 && Tt * c.K1 > 512 && Tt > 1) break;
         if (core_smem<T>(pl, n, Tt, c.spill, sweep1_only, nullptr) > kSmemBudget) break;
@@ -1516,7 +1545,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
   if (N > 1 && !choose_tiles<T>(pl, sweep1_only)) return TT_ERR_UNSUPPORTED;
   // svd and tree shared-memory limits
   for (int n = 0; n + 1 < N && !sweep1_only; ++n)
-    if (smem_svd(pl.core[n].K1, false) > kSmemBudget) return TT_ERR_UNSUPPORTED;
+    if (smem_svd(pl.core[n].K1, false, true) > kSmemBudget) return TT_ERR_UNSUPPORTED;
   for (int n = 1; n < N; ++n)
     if (smem_tree(pl.core[n].R0, pl.core[n].tree.G).bytes > kSmemBudget) return TT_ERR_UNSUPPORTED;
   // workspace layout
@@ -1554,6 +1583,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
     pl.off_tau2 = w.take(sizeof(T) * max_tau2, 256);
   }
   pl.off_part = w.take(sizeof(double) * 4096, 256);
+  pl.off_svdV = w.take(sizeof(double) * B * B, 256);
   pl.off_gscr = w.take(sizeof(T) * std::max<size_t>(pl.gscr_elems, 1), 256);
   pl.total = w.off;
   return TT_OK;
@@ -1887,8 +1917,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.Cnext = C1 + cn.tree.node_off[cn.tree.nlev] * (size_t)B * B;
       a.ldu = B;
       a.status = dstatus;
-      a.precond = smem_svd(K1, true) <= kSmemBudget;
-      const size_t bytes = smem_svd(K1, a.precond != 0);
+      const bool vg = smem_svd(K1, false) > kSmemBudget;
+      a.Vg = vg ? reinterpret_cast<double *>(ws + pl.off_svdV) : nullptr;
+      a.precond = !vg && smem_svd(K1, true) <= kSmemBudget;
+      const size_t bytes = smem_svd(K1, a.precond != 0, vg);
       r = set_smem(k_svd, bytes);
       if (r) return r;
       {

@@ -1,7 +1,8 @@
 """GPU parity of the TSQR tree shapes: nodes that factor their children's triangles in one
 interleaved pass (fan-in 4 up to rank 79, 3 up to 93), nodes that take short children one
-by one (leaves holding fewer rows than the rank), binary trees at higher ranks (up to 117,
-the largest rank whose buffers the planner can place), and applies split over column
+by one (leaves holding fewer rows than the rank), binary trees at higher ranks (117; and
+144, where the leaves' carried tile block and the SVD's rotation accumulator move to global
+memory, as the Hadamard products of rank-12 TTs need), and applies split over column
 chunks -- each against the oracle (ranks
 identical, relative error <= 1e-12 in FP64, <= 1e-6 in fp32x2)."""
 import pytest
@@ -37,7 +38,8 @@ CASES = [
     ([900, 700, 900], [1, 80, 80, 1], 1e-6),      # fan-in 3 at rank 80, apply in column chunks
     ([5000, 37, 5000], [1, 40, 40, 1], 0.0),      # wide middle core (37 slices of 40 rows), eps = 0
     ([300, 260, 300], [1, 100, 100, 1], 1e-6),    # rank 100: leaf buffers spilled to the global scratch
-    ([240, 200, 240], [1, 117, 117, 1], 1e-6),    # the largest rank the planner accepts
+    ([240, 200, 240], [1, 117, 117, 1], 1e-6),    # rank 117: shared memory holds the leaf tile only
+    ([150, 130, 150], [1, 144, 144, 1], 1e-6),    # rank 144: carried tile block and SVD V in global memory
 ]
 
 
