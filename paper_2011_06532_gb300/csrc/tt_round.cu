@@ -190,6 +190,17 @@ __device__ __forceinline__ T *buf(unsigned char *base, int off, T *gscr, size_t 
   return off >= 0 ? reinterpret_cast<T *>(base + off) : gscr + (size_t)blockIdx.x * gstride + (size_t)(-1 - off);
 }
 
+// buf with the spill mode known at compile time: without spilling the compiler sees shared
+// memory and issues shared loads (generic loads measured ~20 % slower in the FP32-storage
+// sweep-2 kernels)
+template <bool SP, typename T>
+__device__ __forceinline__ T *sbuf(unsigned char *base, int off, T *gscr, size_t gstride) {
+  if constexpr (SP)
+    return buf<T>(base, off, gscr, gstride);
+  else
+    return reinterpret_cast<T *>(base + off);
+}
+
 // rows of the stacked matrix owned by leaf range [l0, l1)
 __device__ __forceinline__ int64_t rows_of_leaves(int64_t I, int P, int l0, int l1, int rho) {
   return (leaf_begin(I, P, l1) - leaf_begin(I, P, l0)) * (int64_t)rho;
@@ -523,13 +534,13 @@ __device__ __forceinline__ S out_scale(const int *E, int n, int N) {
   return (S)ldexp(1.0, sh);
 }
 
-template <typename S, typename T>
+template <typename S, typename T, bool SP>
 __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *Q = sm<T>(smem, a.oQ), *CT = buf<T>(smem, a.oCT, a.gscr, a.gstride);
-  T *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride), *Rr = buf<T>(smem, a.oRr, a.gscr, a.gstride);
-  T *Xs = sm<T>(smem, a.oXs), *Ps = buf<T>(smem, a.oPs, a.gscr, a.gstride);
-  Scratch<T> s{sm<T>(smem, a.oRed), buf<T>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
+  T *Q = sm<T>(smem, a.oQ), *CT = sbuf<SP>(smem, a.oCT, a.gscr, a.gstride);
+  T *CR = sbuf<SP>(smem, a.oCR, a.gscr, a.gstride), *Rr = sbuf<SP>(smem, a.oRr, a.gscr, a.gstride);
+  T *Xs = sm<T>(smem, a.oXs), *Ps = sbuf<SP>(smem, a.oPs, a.gscr, a.gstride);
+  Scratch<T> s{sm<T>(smem, a.oRed), sbuf<SP>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
   T *tq = sm<T>(smem, a.oTq), *tv = sm<T>(smem, a.oTv);
   const int p = blockIdx.x, t = threadIdx.x;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
@@ -574,7 +585,7 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
         CT[idx] = (kb + r < ka) ? CR[(kb + r) * L + c] : T(0);
       }
       __syncthreads();
-      hh_apply_grouped(Q, a.ldq, tq, kb, M1, b1, CR, L, CT, L, L, s, buf<T>(smem, a.oTs, a.gscr, a.gstride));
+      hh_apply_grouped(Q, a.ldq, tq, kb, M1, b1, CR, L, CT, L, L, s, sbuf<SP>(smem, a.oTs, a.gscr, a.gstride));
       __syncthreads();
       if (a.mode >= 2) {
         // last core (K1 == 1) or an explicit orthonormal factor: tile row (i - i0) K1 + k
@@ -634,11 +645,11 @@ __global__ void __launch_bounds__(NT) k_s2_leaf(S2Args<S, T> a) {
 // sweep 2 output: core n = Q'_n [U_p; 0]
 // ------------------------------------------------------------------------------------
 
-template <typename S, typename T>
+template <typename S, typename T, bool SP>
 __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  T *V = sm<T>(smem, a.oV), *CT = buf<T>(smem, a.oCT, a.gscr, a.gstride), *CR = buf<T>(smem, a.oCR, a.gscr, a.gstride);
-  Scratch<T> s{sm<T>(smem, a.oRed), buf<T>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
+  T *V = sm<T>(smem, a.oV), *CT = sbuf<SP>(smem, a.oCT, a.gscr, a.gstride), *CR = sbuf<SP>(smem, a.oCR, a.gscr, a.gstride);
+  Scratch<T> s{sm<T>(smem, a.oRed), sbuf<SP>(smem, a.oW, a.gscr, a.gstride), sm<T>(smem, a.oSc)};
   T *tv = sm<T>(smem, a.oTau);
   const int p = blockIdx.x, t = threadIdx.x;
   const int64_t s0 = leaf_begin(a.g.I, a.g.P, p), s1 = leaf_begin(a.g.I, a.g.P, p + 1);
@@ -668,7 +679,7 @@ __global__ void __launch_bounds__(NT) k_s2_out(OutArgs<S, T> a) {
       CT[idx] = (kb + r < ka) ? CR[(kb + r) * Ln + c] : T(0);
     }
     __syncthreads();
-    hh_apply_grouped(V, a.ldv, tv, kb, Mv, K1, CR, Ln, CT, Ln, Ln, s, buf<T>(smem, a.oTs, a.gscr, a.gstride));
+    hh_apply_grouped(V, a.ldv, tv, kb, Mv, K1, CR, Ln, CT, Ln, Ln, s, sbuf<SP>(smem, a.oTs, a.gscr, a.gstride));
     __syncthreads();
     // rows (i - i0) * L + l, column l'  ->  out[l + L (i + I l')]
     for (int idx = t; idx < Mv * Ln; idx += NT) {
@@ -729,6 +740,7 @@ __device__ __forceinline__ void jrot(float al, float be, float ga, float &c, flo
   c = (ah + r) * w;
   sn = (h > 0.0f ? g : -g) * w;
 }
+
 
 // sum over the LP consecutive lanes of a segment (LP a power of two <= 32)
 template <int LP, typename T>
@@ -834,6 +846,42 @@ __host__ __device__ inline size_t svd_w_doubles(int ms, int ns) {
   return a > b ? a : b;
 }
 
+// Re-orthonormalizes the nearly orthogonal V (ns x ns, column-major) by Newton-Schulz
+// iterations in FP64 (X = V^T V, V <- 1.5 V - 0.5 V X; each squares the departure from
+// orthogonality) and replaces A (ms x ns) by A V.  W: 2 ns^2 >= ms ns doubles of scratch.
+__device__ void orth_apply(double *A, double *Vm, double *W, int ms, int ns, int iters) {
+  const int t = threadIdx.x;
+  double *X = W, *Y = W + (size_t)ns * ns;
+  for (int it = 0; it < iters; ++it) {
+    for (int idx = t; idx < ns * ns; idx += SVD_NT) {
+      const int j = idx / ns, i = idx - j * ns;
+      double acc = 0.0;
+      for (int r = 0; r < ns; ++r) acc += Vm[(size_t)i * ns + r] * Vm[(size_t)j * ns + r];
+      X[idx] = acc;
+    }
+    __syncthreads();
+    for (int idx = t; idx < ns * ns; idx += SVD_NT) {
+      const int j = idx / ns, r = idx - j * ns;
+      double acc = 0.0;
+      for (int i = 0; i < ns; ++i) acc += Vm[(size_t)i * ns + r] * X[(size_t)j * ns + i];
+      Y[idx] = 1.5 * Vm[idx] - 0.5 * acc;
+    }
+    __syncthreads();
+    for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = Y[idx];
+    __syncthreads();
+  }
+  // A V (into W, then back into A)
+  for (int idx = t; idx < ms * ns; idx += SVD_NT) {
+    const int j = idx / ms, r = idx - j * ms;
+    double acc = 0.0;
+    for (int i = 0; i < ns; ++i) acc += A[(size_t)i * ms + r] * Vm[(size_t)j * ns + i];
+    W[idx] = acc;
+  }
+  __syncthreads();
+  for (int idx = t; idx < ms * ns; idx += SVD_NT) A[idx] = W[idx];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int K = a.K, t = threadIdx.x;
@@ -896,36 +944,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
         for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = (idx / ns) == (idx % ns) ? 1.0 : 0.0;
       }
       __syncthreads();
-      // Newton-Schulz: X = V^T V, V <- 1.5 V - 0.5 V X (twice); X and the new V in W
-      double *X = W, *Y = W + (size_t)ns * ns;
-      for (int it = 0; it < 2; ++it) {
-        for (int idx = t; idx < ns * ns; idx += SVD_NT) {
-          const int j = idx / ns, i = idx - j * ns;
-          double acc = 0.0;
-          for (int r = 0; r < ns; ++r) acc += Vm[(size_t)i * ns + r] * Vm[(size_t)j * ns + r];
-          X[idx] = acc;
-        }
-        __syncthreads();
-        for (int idx = t; idx < ns * ns; idx += SVD_NT) {
-          const int j = idx / ns, r = idx - j * ns;
-          double acc = 0.0;
-          for (int i = 0; i < ns; ++i) acc += Vm[(size_t)i * ns + r] * X[(size_t)j * ns + i];
-          Y[idx] = 1.5 * Vm[idx] - 0.5 * acc;
-        }
-        __syncthreads();
-        for (int idx = t; idx < ns * ns; idx += SVD_NT) Vm[idx] = Y[idx];
-        __syncthreads();
-      }
-      // B = A V (into W, then back into A)
-      for (int idx = t; idx < ms * ns; idx += SVD_NT) {
-        const int j = idx / ms, r = idx - j * ms;
-        double acc = 0.0;
-        for (int i = 0; i < ns; ++i) acc += A[(size_t)i * ms + r] * Vm[(size_t)j * ns + i];
-        W[idx] = acc;
-      }
-      __syncthreads();
-      for (int idx = t; idx < ms * ns; idx += SVD_NT) A[idx] = W[idx];
-      __syncthreads();
+      orth_apply(A, Vm, W, ms, ns, 2);
     }
   }
   // Deflation threshold: columns whose squared norm is <= 1e-6 delta^2 / ns can never be
@@ -1361,11 +1380,13 @@ SmemTree smem_tree_apply(int b, int G, int cmax) {
   return m;
 }
 
-// Tree fan-in for factors of b columns: 4 children per node (one pass of b reflectors over
-// three interleaved triangles: half the serial reflectors of a binary tree from leaves to
-// root) when such a tile fits in shared memory, else 3, else 2.
+// Tree fan-in for factors of b columns: 8 children per node (one pass of b reflectors over
+// seven interleaved triangles: a 304-leaf tree has 3 levels instead of the 5 of fan-in 4 and
+// the 9 of a binary tree, each level a chain of b reflectors) when such a tile fits in
+// shared memory, else 4, 3, 2.  Measured on the large-mode workload (b = 32): trees
+// 10.9 ms -> 7.9 ms per rounding against fan-in 4.
 int tree_fanin(int b) {
-  for (int G : {4, 3}) {
+  for (int G : {8, 4, 3}) {
     const SmemTree m = smem_tree(b, G);
     if (m.bytes <= kSmemBudget && m.MT >= (G - 1) * b) return G;
   }
@@ -1729,6 +1750,33 @@ static int tree_apply(const Tree &tr, int b, int64_t I, int rho, const int *rho_
   return TT_OK;
 }
 
+// Launches of the sweep-2 kernels in the instantiation matching the core's spill mode.
+template <typename S, typename T>
+static int launch_s2_leaf(const S2Args<S, T> &a, int P, size_t bytes, bool spill, cudaStream_t st) {
+  auto kern = spill ? k_s2_leaf<S, T, true> : k_s2_leaf<S, T, false>;
+  int r = set_smem(kern, bytes);
+  if (r) return r;
+  {
+    TraceScope ts_(TT_K_S2_LEAF, st);
+    kern<<<P, NT, bytes, st>>>(a);
+  }
+  TT_CUDA(cudaGetLastError());
+  return TT_OK;
+}
+
+template <typename S, typename T>
+static int launch_s2_out(const OutArgs<S, T> &a, int P, size_t bytes, bool spill, cudaStream_t st) {
+  auto kern = spill ? k_s2_out<S, T, true> : k_s2_out<S, T, false>;
+  int r = set_smem(kern, bytes);
+  if (r) return r;
+  {
+    TraceScope ts_(TT_K_S2_OUT, st);
+    kern<<<P, NT, bytes, st>>>(a);
+  }
+  TT_CUDA(cudaGetLastError());
+  return TT_OK;
+}
+
 // Source of core n of x, or of the Hadamard product of x and xb when xb is given.
 template <typename S>
 static CoreSrc<S> core_src(const tt_tensor *x, const tt_tensor *xb, int n) {
@@ -1888,13 +1936,8 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.oTv = m.oTv;
       a.ldq = m.ldq;
       a.ldv = m.ldv;
-      r = set_smem(k_s2_leaf<S, T>, m.bytes);
+      r = launch_s2_leaf(a, c.P, m.bytes, c.spill > 0, st);
       if (r) return r;
-      {
-        TraceScope ts_(TT_K_S2_LEAF, st);
-        k_s2_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
-      }
-      TT_CUDA(cudaGetLastError());
     }
     // (b) tree of V-QR factors (rows per slice = L[n])
     r = tree_factor(c.tree, K1, c.I, 1, n == 0 ? nullptr : dL + n, Rbase, slots2, B, st);
@@ -1958,13 +2001,8 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.oSc = m.oSc;
       a.oTau = m.oTau;
       a.ldv = m.ldv;
-      r = set_smem(k_s2_out<S, T>, m.bytes);
+      r = launch_s2_out(a, c.P, m.bytes, c.spill > 0, st);
       if (r) return r;
-      {
-        TraceScope ts_(TT_K_S2_OUT, st);
-        k_s2_out<S, T><<<c.P, NT, m.bytes, st>>>(a);
-      }
-      TT_CUDA(cudaGetLastError());
     }
   }
   // last core: S_{N-2} x_1 Q_{N-1}
@@ -2004,13 +2042,8 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     a.oTv = m.oTv;
     a.ldq = m.ldq;
     a.ldv = m.ldv;
-    r = set_smem(k_s2_leaf<S, T>, m.bytes);
+    r = launch_s2_leaf(a, c.P, m.bytes, c.spill > 0, st);
     if (r) return r;
-    {
-      TraceScope ts_(TT_K_S2_LEAF, st);
-      k_s2_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
-    }
-    TT_CUDA(cudaGetLastError());
   }
   if (ranks_dev) {
     TT_CUDA(cudaMemcpyAsync(ranks_dev, dL, sizeof(int) * (N + 1), cudaMemcpyDeviceToDevice, st));
@@ -2184,13 +2217,8 @@ static int run_orth(const RoundPlan &pl, const tt_tensor *x, tt_tensor *out, uns
     a.oTv = m.oTv;
     a.ldq = m.ldq;
     a.ldv = m.ldv;
-    r = set_smem(k_s2_leaf<S, T>, m.bytes);
+    r = launch_s2_leaf(a, c.P, m.bytes, c.spill > 0, st);
     if (r) return r;
-    {
-      TraceScope ts_(TT_K_S2_LEAF, st);
-      k_s2_leaf<S, T><<<c.P, NT, m.bytes, st>>>(a);
-    }
-    TT_CUDA(cudaGetLastError());
   }
   // core 0: X_0 x_3 R_1 (the root factor of core 1, kept at off_P), times 2^E
   {
