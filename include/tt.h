@@ -233,9 +233,10 @@ int tt_round_batched_async(int32_t count, const tt_tensor *xs, const double *eps
  * Tile autotuning.  Each core of a rounding is split into P leaves (CTAs) over
  * its I_n slices (the leaves of the TSQR tree, Sec. 4.1), each leaf walking its
  * slab in tiles of Tt slices.  Without tuning the library takes P = 2 leaves per
- * SM, but no fewer than 8 b rows of the core's tall-skinny matrix per leaf while
- * that keeps one leaf per SM, at most I_n, and for a batch member at most one
- * leaf per two SMs; and the largest tile that lets two leaves share an SM.  The
+ * SM while each leaf gets at least 16 b rows of the core's tall-skinny matrix, else
+ * one leaf per SM, at most I_n, and for a batch member at most one leaf per two SMs;
+ * with two leaves per SM (and for batch members) the largest tile that lets two
+ * leaves share an SM, with one leaf per SM the largest tile that fits.  The
  * tuner times complete roundings of the given tensor(s) on the GPU and records,
  * per core class (precision, context, I_n, R_{n-1}, R_n and the ranks after the
  * orthogonalization sweep), the fastest (P, Tt) it tried, in a table that every

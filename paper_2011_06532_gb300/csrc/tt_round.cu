@@ -1197,13 +1197,14 @@ Tree make_tree(int P, int G) {
   return tr;
 }
 
-// Leaves of a core whose sweep-1 matrix has `rows` rows and b columns: two per SM, but no
-// fewer than 8 b rows per leaf while that still leaves one leaf per SM (below that the
-// tree's serial reflector chain costs more than the leaf work it spreads); at most I.
+// Leaves of a core whose sweep-1 matrix has `rows` rows and b columns: two per SM while each
+// gets at least 16 b rows, else one per SM (short leaves spend their time in per-tile and
+// per-reflector overheads and add tree nodes: on the paper's Model 1, I_n = 2000 at rank 50,
+// the tuner found one leaf per SM with the largest tiles 16 % faster than 250 leaves); at
+// most I.
 int leaves_for(int64_t I, int64_t rows, int b, int nsm) {
   int64_t target = 2 * (int64_t)nsm;
-  const int64_t by_rows = rows / (8 * (int64_t)std::max(b, 1));
-  if (by_rows < target) target = std::max<int64_t>(nsm, by_rows);
+  if (rows < target * 16 * (int64_t)std::max(b, 1)) target = nsm;
   target = std::min<int64_t>(target, (int64_t)1 << kMaxLev);  // a binary tree holds 2^kMaxLev
   return (int)std::max<int64_t>(1, std::min<int64_t>(I, target));
 }
@@ -1488,7 +1489,7 @@ static size_t core_smem(const RoundPlan &pl, int n, int Tt, int spill, bool swee
 // lets two leaf CTAs share an SM.  Cores whose buffers do not fit even with one slice per
 // tile move their running factor and carried block to a per-leaf global scratch.
 template <typename T>
-static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
+static bool choose_tiles(RoundPlan &pl, bool sweep1_only, int ctx) {
   const int N = pl.N;
   pl.gscr_elems = 0;
   for (int n = 0; n < N; ++n) {
@@ -1509,6 +1510,9 @@ static bool choose_tiles(RoundPlan &pl, bool sweep1_only) {
     c.Tt = best;
     if (c.Tt_want > 0) {
       c.Tt = std::min(best, c.Tt_want);
+    } else if (ctx == kCtxSolo && c.P <= pl.nsm) {
+      // one leaf per SM: the largest tile that fits
+      c.Tt = best;
     } else {
       // heuristic: the largest tile that lets two leaves share an SM
       for (int Tt = best; Tt >= 1; --Tt) {
@@ -1563,7 +1567,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
     }
     c.tree = make_tree(c.P, std::min(tree_fanin(c.R0), tree_fanin(c.K1)));
   }
-  if (N > 1 && !choose_tiles<T>(pl, sweep1_only)) return TT_ERR_UNSUPPORTED;
+  if (N > 1 && !choose_tiles<T>(pl, sweep1_only, ctx)) return TT_ERR_UNSUPPORTED;
   // svd and tree shared-memory limits
   for (int n = 0; n + 1 < N && !sweep1_only; ++n)
     if (smem_svd(pl.core[n].K1, false, true) > kSmemBudget) return TT_ERR_UNSUPPORTED;
