@@ -313,7 +313,40 @@ def run_variants(args):
     torch.cuda.empty_cache()
     out["hadamard_pipeline"] = run_pipeline(args)
     out["paper_model1"] = run_model1(args)
+    out["small_N6_I32_R10"] = run_small(args)
     return out
+
+
+def run_small(args):
+    """The small workload (N=6, I_n=32, formal ranks 10 -> 5, eps=1e-6, FP64): one rounding at
+    a time (launch- and latency-bound: each call queues ~130 small launches and synchronizes
+    once for the ranks) and 512 copies rounded as one graph-captured batch."""
+    import torch
+
+    import paper_2011_06532_gb300 as ttgb
+    import ttgen
+
+    (Y, Yp), eps = ttgen.config_small()
+    X = ttgb.tt_add(ttgb.from_host(Y.I, Y.R, Y.cores), ttgb.from_host(Yp.I, Yp.R, Yp.cores))
+    y = ttgb.tt_round(X, eps)
+    t1 = _time(lambda: ttgb.tt_round(X, eps), reps=200)
+    copies = 512
+    xs = [ttgb.DeviceTT(list(X.I), list(X.R), [c.clone() for c in X.cores]) for _ in range(copies)]
+    b = ttgb.Batch(xs, [eps] * copies, "fp64")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b.enqueue(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.enqueue(s)
+    tb = _time(g.replay, reps=5)
+    same = all(o.R == y.R for o in b.outputs())
+    del b, g, xs
+    torch.cuda.empty_cache()
+    return {"ranks": y.R, "single_tt_rounds_per_s": 1.0 / t1, "single_ms": t1 * 1e3,
+            "graph_batch": {"copies": copies, "tt_rounds_per_s": copies / tb, "ms": tb * 1e3, "ranks_equal": same}}
 
 
 def run_batched_recipe(args):

@@ -10,6 +10,7 @@
  *   tt_norm      Sec. 3.2.4 (norm through orthonormalization)
  *   tt_orthonormalize  Alg. 1 / Alg. 5 and the left-hand mirror (Sec. 3.4)
  *   tt_round_ordered   the RLR and LRL orderings of rounding (Sec. 3.4, 4.3.2)
+ *   tt_round_sharded   rounding of a tensor distributed over shards (Sec. 3.1, 3.3)
  *
  * Tensor layout.  A TT tensor X has N >= 1 cores; core n (0-based) is an
  * R[n] x I[n] x R[n+1] array with R[0] = R[N] = 1 (Sec. 2.1).  Entry (a, i, b)
@@ -57,8 +58,9 @@ typedef enum {
   TT_ERR_WORKSPACE = 2,   /* workspace missing or smaller than the size query returned */
   TT_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   TT_ERR_NUMERICAL = 4,   /* non-finite values met, or an SVD did not converge */
-  TT_ERR_UNSUPPORTED = 6  /* a rank above TT_MAX_RANK, or a shape whose buffers the
+  TT_ERR_UNSUPPORTED = 6, /* a rank above TT_MAX_RANK, or a shape whose buffers the
                              planner cannot place */
+  TT_ERR_COMM = 7         /* the all-gather callback of a sharded call failed */
 } tt_status;
 
 typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
@@ -171,6 +173,67 @@ int tt_round_hadamard_workspace_size(const tt_tensor *a, const tt_tensor *b, int
  */
 int tt_round_hadamard(const tt_tensor *a, const tt_tensor *b, double eps, int precision, tt_tensor *out,
                       void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Sharded rounding: one tensor distributed over `world_size` shards (processes,
+ * one per GPU), each owning a contiguous range of the slices of every core -- the
+ * 1 x P x 1 distribution of Sec. 3.1 (Fig. 2): core n of shard p holds slices
+ * [begin_p, end_p) of mode n, begin_p = floor(p I_n / world_size) (tt_shard_range),
+ * as an R_{n-1} x (end_p - begin_p) x R_n core in the layout above.
+ *
+ * Every tall-skinny QR of Alg. 6 then spans the shards (Sec. 3.3): each shard
+ * factors its row block with the single-GPU kernels, the shards all-gather their
+ * b x b triangular factors, and every shard factors the same tree over the
+ * gathered factors (the redundant root of the butterfly TSQR, Alg. 3, for any
+ * number of shards).  Applying Q (Alg. 4) then needs no communication: each shard
+ * applies the shard-level tree and keeps its own block.  A rounding exchanges one
+ * payload per tall-skinny QR (2(N-1) of them) plus one before any work (the
+ * arguments of all shards must agree) and one at the end (so that every shard
+ * returns the same status): 2N all-gathers per call, in the same order on every
+ * shard, whatever fails.  The first payload is a 16-byte header; the others are
+ * 16 + 8 b_max^2 bytes, b_max the largest input rank.
+ */
+typedef int (*tt_allgather_fn)(const void *send, void *recv, size_t bytes, void *ctx);
+
+typedef struct {
+  int32_t rank;             /* this shard, 0 <= rank < world_size */
+  int32_t world_size;       /* number of shards, 1..1024 */
+  const int64_t *I_global;  /* host array [N]: mode sizes of the whole tensor, each
+                               >= world_size; x->I[n] must be the length of this
+                               shard's range of mode n */
+  tt_allgather_fn allgather;/* gathers `bytes` from every shard's `send` (host memory)
+                               into `recv` (world_size * bytes, shard p's at offset
+                               p * bytes) on every shard; returns 0 on success.  Called
+                               from the thread that called tt_round_sharded */
+  void *ctx;                /* passed to allgather */
+} tt_shard;
+
+/* Range [*begin, *end) of the slices of a mode of size I that shard `rank` of
+ * `world_size` owns.  Host only; TT_ERR_INVALID_ARG unless 1 <= world_size <= I,
+ * world_size <= 1024 and 0 <= rank < world_size. */
+int tt_shard_range(int64_t I, int32_t world_size, int32_t rank, int64_t *begin, int64_t *end);
+
+/* Workspace bytes of tt_round_sharded on this shard (x is the local tensor). */
+int tt_round_sharded_workspace_size(const tt_tensor *x, int precision, const tt_shard *shard, size_t *bytes);
+
+/*
+ * TT rounding (Alg. 2 / Alg. 6, RLR ordering) of the tensor whose shard `rank`
+ * is x.  Every shard calls this with the same eps, precision, I_global, ranks and
+ * dtype; on return out (as in tt_round, local mode sizes) holds this shard's
+ * slices of the rounded cores and out->R the new ranks, the same on every shard.
+ * The result equals tt_round's on the whole tensor up to rounding errors (the
+ * reduction tree differs).  A shard whose own arguments are wrong (x->I not its
+ * range, workspace short, cores not device-accessible) still takes part in the
+ * first all-gather and every shard returns the first such error in rank order;
+ * arguments that disagree between shards return TT_ERR_INVALID_ARG on all; a
+ * failed allgather call returns TT_ERR_COMM (after the first all-gather, the
+ * remaining all-gathers of the call are still made, so that the shards stay in
+ * step).  A NULL shard, a NULL callback or a rank outside [0, world_size) returns
+ * TT_ERR_INVALID_ARG without calling allgather.  world_size 1 is tt_round.
+ * Synchronizes `stream` at every all-gather.
+ */
+int tt_round_sharded(const tt_tensor *x, double eps, int precision, const tt_shard *shard, tt_tensor *out,
+                     void *workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Orthonormalization with explicit factors (Alg. 1, parallel form Alg. 5; the

@@ -22,7 +22,8 @@ from . import _native
 from ._native import build  # noqa: F401  (re-export)
 
 __all__ = ["DeviceTT", "Batch", "build", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard", "tt_dot", "tt_norm",
-           "tt_orthonormalize", "tt_round_hadamard", "TTError", "from_host", "to_host", "trace", "trace_read"]
+           "tt_orthonormalize", "tt_round_hadamard", "tt_round_sharded", "shard_range", "dist_allgather", "TTError",
+           "from_host", "to_host", "trace", "trace_read"]
 
 _DTYPES = {torch.float64: 0, torch.float32: 1}
 # tt_precision: "default" (fp64 for float64 cores, fp32x2 for float32), "fp64", "fp32x2", "fp32"
@@ -354,6 +355,89 @@ def tt_hadamard(a: DeviceTT, b: DeviceTT, stream=None) -> DeviceTT:
     o = _Desc(a.I, R, out, a.dtype)
     _check(lib.tt_hadamard(da.ref, db.ref, o.ref, _stream(stream)), "tt_hadamard")
     return DeviceTT(list(a.I), o.ranks(), out)
+
+
+def shard_range(I: int, world: int, rank: int):
+    """Slices [begin, end) of a mode of size I owned by shard `rank` of `world` (the 1 x P x 1
+    distribution of Sec. 3.1): begin = floor(rank I / world)."""
+    lib = _native.load()
+    b, e = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.tt_shard_range(int(I), int(world), int(rank), ctypes.byref(b), ctypes.byref(e)), "tt_shard_range")
+    return int(b.value), int(e.value)
+
+
+class _Gather:
+    """ctypes adapter of a Python all-gather fn(send, recv) over uint8 numpy views of the
+    library's host buffers; an exception raised by fn becomes status TT_ERR_COMM in the
+    library and is raised again after the call."""
+
+    def __init__(self, fn, world: int):
+        import numpy as np
+
+        self.fn, self.world, self.error = fn, world, None
+
+        def cb(send, recv, nbytes, ctx):
+            try:
+                s = np.ctypeslib.as_array((ctypes.c_ubyte * nbytes).from_address(send))
+                r = np.ctypeslib.as_array((ctypes.c_ubyte * (nbytes * self.world)).from_address(recv))
+                self.fn(s, r)
+                return 0
+            except BaseException as e:  # noqa: BLE001 -- reported after the call
+                if self.error is None:
+                    self.error = e
+                return 1
+
+        self.c = _native.ALLGATHER_FN(cb)
+
+
+def dist_allgather(group=None):
+    """An all-gather for tt_round_sharded over a torch.distributed process group: the payload
+    is gathered as a uint8 tensor (host tensors for gloo, tensors of the current CUDA device
+    for NCCL) in rank order."""
+    import torch.distributed as dist
+
+    def fn(send, recv):
+        world = dist.get_world_size(group)
+        t = torch.from_numpy(send.copy())
+        if dist.get_backend(group) == "nccl":
+            t = t.cuda()
+        parts = [torch.empty_like(t) for _ in range(world)]
+        dist.all_gather(parts, t, group=group)
+        recv[:] = torch.cat(parts).cpu().numpy()
+
+    return fn
+
+
+def tt_round_sharded(x: DeviceTT, eps: float, I_global: Sequence[int], rank: int, world: int, allgather,
+                     precision: str = "default", stream=None, workspace: Optional[torch.Tensor] = None) -> DeviceTT:
+    """TT rounding (Alg. 2 / Alg. 6) of a tensor distributed over `world` shards: x is shard
+    `rank`, holding slices shard_range(I_global[n], world, rank) of every core.  Every shard
+    calls this with the same eps, precision, I_global and ranks; allgather(send, recv) gathers
+    the bytes of send (uint8 numpy array) from every shard into recv (world times longer, in
+    rank order), e.g. dist_allgather().  Returns this shard's slices of the rounded tensor
+    (ranks equal on every shard).  The workspace is this call's own (shards on threads of one
+    process do not share one)."""
+    _validate(x)
+    lib = _native.load()
+    dev = x.cores[0].device
+    prec = PRECISIONS[precision]
+    d = _Desc(x.I, x.R, x.cores, x.dtype)
+    g = _Gather(allgather, world)
+    Ig = (ctypes.c_int64 * x.N)(*[int(v) for v in I_global])
+    sh = _native.TTShard(int(rank), int(world), Ig, g.c, None)
+    n = ctypes.c_size_t(0)
+    _check(lib.tt_round_sharded_workspace_size(d.ref, prec, ctypes.byref(sh), ctypes.byref(n)),
+           "tt_round_sharded_workspace_size")
+    ws = workspace if workspace is not None else torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+    out = [torch.empty(s, dtype=x.dtype, device=dev) for s in x.core_sizes()]
+    o = _Desc(x.I, [1] * (x.N + 1), out, x.dtype)
+    st = lib.tt_round_sharded(d.ref, float(eps), prec, ctypes.byref(sh), o.ref, ctypes.c_void_p(ws.data_ptr()),
+                              ctypes.c_size_t(ws.numel()), _stream(stream))
+    if g.error is not None:
+        raise TTError(st, "tt_round_sharded (all-gather)") from g.error
+    _check(st, "tt_round_sharded")
+    R = o.ranks()
+    return DeviceTT(list(x.I), R, [out[k][: R[k] * x.I[k] * R[k + 1]] for k in range(x.N)])
 
 
 def tt_round_hadamard(a: DeviceTT, b: DeviceTT, eps: float, stream=None, precision: str = "default") -> DeviceTT:

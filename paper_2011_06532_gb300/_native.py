@@ -72,6 +72,20 @@ class TTTensor(ctypes.Structure):
     ]
 
 
+# int (*)(const void *send, void *recv, size_t bytes, void *ctx)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class TTShard(ctypes.Structure):
+    _fields_ = [
+        ("rank", ctypes.c_int32),
+        ("world_size", ctypes.c_int32),
+        ("I_global", ctypes.POINTER(ctypes.c_int64)),
+        ("allgather", ALLGATHER_FN),
+        ("ctx", ctypes.c_void_p),
+    ]
+
+
 EXPORTS = [
     "tt_round_workspace_size", "tt_round", "tt_round_batched", "tt_add", "tt_hadamard",
     "tt_dot_workspace_size", "tt_dot", "tt_norm_workspace_size", "tt_norm", "tt_status_string",
@@ -80,6 +94,7 @@ EXPORTS = [
     "tt_tune_export", "tt_tune_import", "tt_tune_clear", "tt_tune_generation",
     "tt_round_ordered_workspace_size", "tt_round_ordered", "tt_orthonormalize_workspace_size", "tt_orthonormalize",
     "tt_round_hadamard_workspace_size", "tt_round_hadamard",
+    "tt_shard_range", "tt_round_sharded_workspace_size", "tt_round_sharded",
 ]
 KERNEL_KINDS = ["s1_leaf", "tree_factor", "tree_apply", "s2_leaf", "s2_out", "svd", "add", "hadamard", "dot", "misc"]
 
@@ -124,6 +139,10 @@ def load(path: str | None = None):
         "tt_orthonormalize": [T, ctypes.c_int, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
         "tt_round_hadamard_workspace_size": [T, T, ctypes.c_int, sz],
         "tt_round_hadamard": [T, T, ctypes.c_double, ctypes.c_int, T, vp, ctypes.c_size_t, vp],
+        "tt_shard_range": [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                           ctypes.POINTER(ctypes.c_int64)],
+        "tt_round_sharded_workspace_size": [T, ctypes.c_int, ctypes.POINTER(TTShard), sz],
+        "tt_round_sharded": [T, ctypes.c_double, ctypes.c_int, ctypes.POINTER(TTShard), T, vp, ctypes.c_size_t, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)

@@ -205,6 +205,91 @@ int tt_round_ordered(const tt_tensor *x, double eps, int precision, int order, t
 }
 
 namespace {
+constexpr int kMaxShards = 1024;
+
+// first slice of shard p of W over a mode of size I (the leaf partition of the kernels)
+int64_t shard_begin(int64_t I, int W, int p) { return (int64_t)p * I / W; }
+int64_t shard_len(int64_t I, int W, int p) { return shard_begin(I, W, p + 1) - shard_begin(I, W, p); }
+
+bool valid_shard(const tt_shard *s) {
+  return s && s->allgather && s->I_global && s->world_size >= 1 && s->world_size <= kMaxShards && s->rank >= 0 &&
+         s->rank < s->world_size;
+}
+
+// FNV-1a digest of the arguments every shard must share.
+struct Digest {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  }
+};
+
+// This shard's own argument checks (0 if fine) and the digest of the shared ones.
+int shard_checks(const tt_tensor *x, double eps, int precision, const tt_shard *s, const tt_tensor *out, int *prec,
+                 uint64_t *check) {
+  *check = 0;
+  *prec = -1;
+  if (!valid_tensor(x)) return TT_ERR_INVALID_ARG;
+  Digest d;
+  d.add(&x->N, sizeof x->N);
+  d.add(&x->dtype, sizeof x->dtype);
+  d.add(&precision, sizeof precision);
+  d.add(&eps, sizeof eps);
+  d.add(&s->world_size, sizeof s->world_size);
+  d.add(s->I_global, sizeof(int64_t) * x->N);
+  d.add(x->R, sizeof(int64_t) * (x->N + 1));
+  *check = d.h;
+  for (int n = 0; n < x->N; ++n) {
+    if (s->I_global[n] < s->world_size) return TT_ERR_INVALID_ARG;
+    if (x->I[n] != shard_len(s->I_global[n], s->world_size, s->rank)) return TT_ERR_INVALID_ARG;
+  }
+  if (!valid_out(x, out) || !(eps >= 0.0) || !isfinite(eps)) return TT_ERR_INVALID_ARG;
+  *prec = resolve_prec(x, precision);
+  if (*prec < 0) return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  if (!cores_accessible(x) || !cores_accessible(out)) return TT_ERR_INVALID_ARG;
+  return TT_OK;
+}
+}  // namespace
+
+int tt_shard_range(int64_t I, int32_t world_size, int32_t rank, int64_t *begin, int64_t *end) {
+  if (!begin || !end || world_size < 1 || world_size > kMaxShards || I < world_size || rank < 0 || rank >= world_size)
+    return TT_ERR_INVALID_ARG;
+  *begin = shard_begin(I, world_size, rank);
+  *end = shard_begin(I, world_size, rank + 1);
+  return TT_OK;
+}
+
+int tt_round_sharded_workspace_size(const tt_tensor *x, int precision, const tt_shard *shard, size_t *bytes) {
+  if (!valid_tensor(x) || !bytes || !valid_shard(shard)) return TT_ERR_INVALID_ARG;
+  if (shard->world_size == 1) return tt_round_workspace_size(x, precision, bytes);
+  const int prec = resolve_prec(x, precision);
+  if (prec < 0) return TT_ERR_INVALID_ARG;
+  for (int n = 0; n < x->N; ++n)
+    if (shard->I_global[n] < shard->world_size ||
+        x->I[n] != shard_len(shard->I_global[n], shard->world_size, shard->rank))
+      return TT_ERR_INVALID_ARG;
+  if (!ranks_supported(x)) return TT_ERR_UNSUPPORTED;
+  return ttgb::round_sharded_workspace(x, prec, shard->world_size, shard->rank, shard->I_global, bytes);
+}
+
+int tt_round_sharded(const tt_tensor *x, double eps, int precision, const tt_shard *shard, tt_tensor *out,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+  if (!valid_shard(shard)) return TT_ERR_INVALID_ARG;
+  if (shard->world_size == 1) {
+    if (!valid_tensor(x)) return TT_ERR_INVALID_ARG;
+    for (int n = 0; n < x->N; ++n)
+      if (shard->I_global[n] != x->I[n]) return TT_ERR_INVALID_ARG;
+    return tt_round(x, eps, precision, out, workspace, workspace_bytes, stream);
+  }
+  int prec = -1;
+  uint64_t check = 0;
+  const int local = shard_checks(x, eps, precision, shard, out, &prec, &check);
+  return ttgb::round_sharded_run(x, eps, prec, shard, local, check, out, workspace, workspace_bytes, as_stream(stream));
+}
+
+namespace {
 // Shape of the Hadamard product of a and b (ranks multiply), cores unset.
 struct ProductShape {
   std::vector<int64_t> R;
@@ -510,6 +595,7 @@ const char *tt_status_string(int status) {
     case TT_ERR_CUDA: return "CUDA runtime error";
     case TT_ERR_NUMERICAL: return "non-finite values or SVD not converged";
     case TT_ERR_UNSUPPORTED: return "unsupported size (rank above the supported maximum)";
+    case TT_ERR_COMM: return "the all-gather of a sharded call failed";
     default: return "unknown status";
   }
 }

@@ -52,6 +52,9 @@ int round_hadamard_run(const tt_tensor *a, const tt_tensor *b, const tt_tensor *
 int round_lrl_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes,
                   cudaStream_t st);
 int norm_run(const tt_tensor *x, double *result, void *ws, size_t ws_bytes, cudaStream_t st);
+int round_sharded_workspace(const tt_tensor *x, int prec, int world, int rank, const int64_t *Ig, size_t *bytes);
+int round_sharded_run(const tt_tensor *x, double eps, int prec, const tt_shard *shard, int local_status,
+                      uint64_t check, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st);
 
 int add_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStream_t st);
 int hadamard_run(const tt_tensor *a, const tt_tensor *b, tt_tensor *out, cudaStream_t st);

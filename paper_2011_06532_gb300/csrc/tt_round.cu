@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 #include "tt.h"
@@ -753,7 +754,11 @@ __device__ __forceinline__ T seg_sum(T v) {
 // Round-robin one-sided Jacobi on A (ms x ns, column-major), accumulating the rotations
 // into V (ns x ns, column-major).  pos holds 2 * (ns + 2) ints, flag 1 int.  Returns
 // whether a sweep completed without rotating.  Pairs whose two columns both have squared
-// norms <= neg2 are left alone (deflation of negligible columns).
+// norms <= neg2 are left alone (deflation of negligible columns), and so are pairs with one
+// column of squared norm <= neg1: its coupling g <= |c1| |c2| to the other column moves the
+// pair's eigenvalues by at most g^2 / gap <= neg1 and the other column's direction by at
+// most sqrt(neg1) in norm, so such a column (rounding noise of a rank-deficient factor)
+// cannot keep the sweeps going.
 // Each pair is handled by a segment of LP = 8 lanes (4 pairs per warp): on GB300 an FP64
 // warp instruction costs the FP64 unit the same time whatever its active lanes, so the
 // per-pair dot products, reductions and rotation angle are packed four to an instruction.
@@ -762,7 +767,7 @@ __device__ __forceinline__ T seg_sum(T v) {
 // square of this one's), so the sweep that would only confirm convergence is skipped.
 // pos holds 2 * (ns + 2) ints, flag 2 ints.
 template <typename T>
-__device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2,
+__device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2, T neg1,
                        bool quad_stop = false, bool accumulate_v = true) {
   constexpr int LP = 8, PW = 32 / LP;  // lanes per pair, pairs per warp
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
@@ -806,7 +811,9 @@ __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, i
         al = seg_sum<LP>(al);
         be = seg_sum<LP>(be);
         ga = seg_sum<LP>(ga);
-        if (!live || ga == T(0) || ga * ga <= tol2 * al * be || (al <= neg2 && be <= neg2)) continue;
+        if (!live || ga == T(0) || ga * ga <= tol2 * al * be || (al <= neg2 && be <= neg2) || al <= neg1 ||
+            be <= neg1)
+          continue;
         if (quad_stop && sl == 0) atomicMax(flag + 1, __float_as_int((float)((ga / al) * (ga / be))));
         T cs, sn;
         jrot(al, be, ga, cs, sn);
@@ -930,7 +937,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
       for (int idx = t; idx < ns * ns; idx += SVD_NT) V32[idx] = (idx / ns) == (idx % ns) ? 1.0f : 0.0f;
       __syncthreads();
       // columns below FP32 resolution relative to the largest entry carry no information here
-      jacobi<float>(A32, V32, ms, ns, pos, flag, 4e-6f, 20, 1e-12f * (float)ms);
+      jacobi<float>(A32, V32, ms, ns, pos, flag, 4e-6f, 20, 1e-12f * (float)ms, 0.0f);
       int *bad = flag + 2;
       if (t == 0) *bad = 0;
       __syncthreads();
@@ -949,8 +956,10 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   }
   // Deflation threshold: columns whose squared norm is <= 1e-6 delta^2 / ns can never be
   // kept by the rank rule and their total mass stays exact in the tails (sum of squared
-  // column norms), so pairs of two such columns need no rotation.  For n = 0, delta is
-  // taken from ||A||_F (= ||X||, Sec. 2.3) only to set this threshold.
+  // column norms), so pairs of two such columns need no rotation; a column of squared norm
+  // <= 1e-9 delta^2 / ns needs none with any column (it moves a kept direction by at most
+  // 3.2e-5 delta / sqrt(ns), an error below 3.2e-5 eps ||X|| / sqrt(N - 1) in the result).
+  // For n = 0, delta is taken from ||A||_F (= ||X||, Sec. 2.3) only to set this threshold.
   {
     double f2 = 0.0;
     if (a.n == 0)
@@ -975,7 +984,8 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   __syncthreads();
   // A square root factor (not wide) needs no rotation accumulator: the next core's factor
   // V Sigma equals R^T U (R = U Sigma V^T) and is formed from R and U_hat below.
-  const bool converged = jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, true, wide);
+  const bool converged =
+      jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, 1e-3 * neg2, true, wide);
   // singular values
   const int lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   for (int c = warp; c < ns; c += nwarp) {
@@ -1404,13 +1414,16 @@ size_t smem_svd(int K, bool precond, bool vglobal = false) {
 
 struct CorePlan {
   int64_t I = 0;
+  int64_t Ig = 0;      // mode size of the whole tensor (I unless sharded)
   int R0 = 1, R1 = 1;  // input ranks
   int K0 = 1, K1 = 1;  // ranks after sweep 1
   int P = 1, Tt = 1;
   int Tt_want = 0;     // tuned tile (0 = heuristic); clamped to what fits
   int spill = 0;  // 1: running factor / carried blocks in global scratch, 2: also the tile block CT
   Tree tree;
+  Tree stree;          // sharded: tree over the shards' roots (one leaf per shard)
   size_t refl_off = 0, tau_off = 0, slot_off = 0;  // sweep-1 storage (n >= 1)
+  size_t sslot_off = 0;  // sharded: sweep-1 slots of the shard-level tree (n >= 1)
 };
 
 TileKey core_key(const CorePlan &c, int prec, int ctx) {
@@ -1442,6 +1455,17 @@ struct RoundPlan {
   size_t max_nodes = 0, max_slots = 0;
   size_t total = 0;
   int tree_MT[TT_MAX_RANK + 1];
+  // sharded rounding: shard-level tree levels (R, and C for the two applies), the
+  // V-QR slots of the shard-level tree
+  int world = 1, rank = 0;
+  size_t off_Rs = 0, off_Cs1 = 0, off_Cs2 = 0, off_sslots2 = 0;
+};
+
+// Slab of a sharded tensor: shard `rank` of `world` owns slices
+// [leaf_begin(Ig, world, rank), leaf_begin(Ig, world, rank + 1)) of every mode.
+struct ShardGeom {
+  int world = 1, rank = 0;
+  const int64_t *Ig = nullptr;
 };
 
 int device_sm_count() {
@@ -1530,7 +1554,8 @@ static bool choose_tiles(RoundPlan &pl, bool sweep1_only, int ctx) {
 }
 
 template <typename T>
-static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int prec, int ctx) {
+static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int prec, int ctx,
+                     const ShardGeom *sg = nullptr) {
   const int N = x->N;
   pl.N = N;
   pl.keep_q = !sweep1_only;
@@ -1541,15 +1566,16 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
   for (int n = 0; n < N; ++n) {
     CorePlan &c = pl.core[n];
     c.I = x->I[n];
+    c.Ig = sg ? sg->Ig[n] : c.I;
     c.R0 = (int)x->R[n];
     c.R1 = (int)x->R[n + 1];
     pl.bmax = std::max(pl.bmax, std::max(c.R0, c.R1));
   }
-  // ranks after the right-to-left sweep: K_n = min(R_n, I_n K_{n+1})
+  // ranks after the right-to-left sweep: K_n = min(R_n, I_n K_{n+1}), I_n of the whole tensor
   pl.core[N - 1].K1 = 1;
   for (int n = N - 1; n >= 1; --n) {
     CorePlan &c = pl.core[n];
-    c.K0 = (int)std::min<int64_t>(c.R0, c.I * c.K1);
+    c.K0 = (int)std::min<int64_t>(c.R0, c.Ig * c.K1);
     pl.core[n - 1].K1 = c.K0;
   }
   pl.core[0].K0 = 1;
@@ -1566,6 +1592,7 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
       c.Tt_want = tc.Tt;
     }
     c.tree = make_tree(c.P, std::min(tree_fanin(c.R0), tree_fanin(c.K1)));
+    if (sg) c.stree = make_tree(sg->world, c.tree.G);
   }
   if (N > 1 && !choose_tiles<T>(pl, sweep1_only, ctx)) return TT_ERR_UNSUPPORTED;
   // svd and tree shared-memory limits
@@ -1607,6 +1634,27 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
     pl.off_refl2 = w.take(sizeof(T) * max_refl2, 256);
     pl.off_tau2 = w.take(sizeof(T) * max_tau2, 256);
   }
+  if (sg) {
+    pl.world = sg->world;
+    pl.rank = sg->rank;
+    size_t snodes = 1, sslots2 = 1;
+    for (int n = 0; n < N; ++n) {
+      CorePlan &c = pl.core[n];
+      snodes = std::max(snodes, c.stree.nnodes);
+      if (n >= 1) {
+        const SmemTree st = smem_tree(c.R0, c.stree.G);
+        c.sslot_off = w.take(sizeof(double) * c.stree.nslots * ((size_t)c.R0 * c.R0 + (size_t)st.nchunk * c.R0), 256);
+      }
+      if (n < N - 1) {
+        const SmemTree st = smem_tree(c.K1, c.stree.G);
+        sslots2 = std::max(sslots2, c.stree.nslots * ((size_t)c.K1 * c.K1 + (size_t)st.nchunk * c.K1));
+      }
+    }
+    pl.off_Rs = w.take(sizeof(double) * snodes * B * B, 256);
+    pl.off_Cs1 = w.take(sizeof(double) * snodes * B * B, 256);
+    pl.off_Cs2 = w.take(sizeof(double) * snodes * B * B, 256);
+    pl.off_sslots2 = w.take(sizeof(double) * sslots2, 256);
+  }
   pl.off_part = w.take(sizeof(double) * 4096, 256);
   pl.off_svdV = w.take(sizeof(double) * B * B, 256);
   pl.off_gscr = w.take(sizeof(T) * std::max<size_t>(pl.gscr_elems, 1), 256);
@@ -1615,11 +1663,12 @@ static int make_plan(const tt_tensor *x, RoundPlan &pl, bool sweep1_only, int pr
 }
 
 // compute type of each precision: FP64 -> double, FP32X2 -> df32 (pairs of floats), FP32 -> float
-static int plan_for(const tt_tensor *x, int prec, RoundPlan &pl, bool sweep1_only, int ctx = kCtxSolo) {
+static int plan_for(const tt_tensor *x, int prec, RoundPlan &pl, bool sweep1_only, int ctx = kCtxSolo,
+                    const ShardGeom *sg = nullptr) {
   switch (prec) {
-    case TT_PREC_FP64: return make_plan<double>(x, pl, sweep1_only, prec, ctx);
-    case TT_PREC_FP32X2: return make_plan<df32>(x, pl, sweep1_only, prec, ctx);
-    case TT_PREC_FP32: return make_plan<float>(x, pl, sweep1_only, prec, ctx);
+    case TT_PREC_FP64: return make_plan<double>(x, pl, sweep1_only, prec, ctx, sg);
+    case TT_PREC_FP32X2: return make_plan<df32>(x, pl, sweep1_only, prec, ctx, sg);
+    case TT_PREC_FP32: return make_plan<float>(x, pl, sweep1_only, prec, ctx, sg);
     default: return TT_ERR_INVALID_ARG;
   }
 }
@@ -1781,6 +1830,95 @@ static int launch_s2_out(const OutArgs<S, T> &a, int P, size_t bytes, bool spill
   return TT_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// sharded rounding: one shard's side of the all-gathers.  Each shard owns a slab of
+// every core (the 1 x P x 1 distribution of Sec. 3.1); every tall-skinny QR reduces
+// the shards' local roots by an all-gather and a tree over the gathered roots that
+// every shard factors alike (the redundant root of the butterfly TSQR, Sec. 3.3.1),
+// so applying Q needs no messages (Sec. 3.3.2).  Tree levels keep R nodes b*b apart
+// (b x b, leading dimension b) and C nodes b*B apart (b rows, leading dimension B).
+// ------------------------------------------------------------------------------------
+struct ShardHeader {
+  int32_t status;  // the sender's status (0 = fine)
+  int32_t seq;     // index of this all-gather within the call
+  uint64_t check;  // digest of the call's arguments (first all-gather), else 0
+};
+
+class Shard {
+ public:
+  Shard(const tt_shard *s, int B) : s_(s), B_(B), block_(sizeof(double) * (size_t)B * B) {}
+  int seq() const { return seq_; }
+
+  // All-gather of this shard's header and, after the first exchange, of `elems` <= B*B
+  // doubles (device src; zeros if null) into dst (device, world runs of `elems` doubles
+  // back to back in rank order; skipped if null).  Every payload after the first has the
+  // same size (header and B*B doubles).  Returns the status every shard agrees on: the
+  // first nonzero in rank order, where a shard out of step or with another digest than
+  // shard 0 counts as TT_ERR_INVALID_ARG; TT_ERR_COMM if the callback fails.
+  int exchange(const double *src, double *dst, size_t elems, int status, uint64_t check, bool header_only,
+               cudaStream_t st) {
+    const size_t bytes = sizeof(ShardHeader) + (header_only ? 0 : block_);
+    const size_t run = sizeof(double) * elems;
+    const int W = s_->world_size;
+    send_.assign(bytes, 0);
+    recv_.assign(bytes * W, 0);
+    ShardHeader h{status, seq_++, check};
+    if (!h.status && run > block_) h.status = TT_ERR_INVALID_ARG;
+    if (!h.status) {
+      // the synchronization also surfaces a fault of the work queued so far
+      if (src && !header_only && run &&
+          cudaMemcpyAsync(send_.data() + sizeof h, src, run, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        h.status = TT_ERR_CUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) h.status = TT_ERR_CUDA;
+    }
+    std::memcpy(send_.data(), &h, sizeof h);
+    if (s_->allgather(send_.data(), recv_.data(), bytes, s_->ctx) != 0) return TT_ERR_COMM;
+    ShardHeader q0;
+    std::memcpy(&q0, recv_.data(), sizeof q0);
+    for (int p = 0; p < W; ++p) {
+      ShardHeader q;
+      std::memcpy(&q, recv_.data() + (size_t)p * bytes, sizeof q);
+      if (q.status) return q.status;
+      if (q.seq != q0.seq || q.check != q0.check) return TT_ERR_INVALID_ARG;
+    }
+    if (dst && !header_only && run)
+      TT_CUDA(cudaMemcpy2DAsync(dst, run, recv_.data() + sizeof h, bytes, run, W, cudaMemcpyHostToDevice, st));
+    return TT_OK;
+  }
+
+  // Shard-level factorization: gathers every shard's local root (a b x b node at
+  // local_root) as the leaves of c.stree (level 0 of Rs) and factors that tree; *root is
+  // its root (the R factor of the whole tall-skinny matrix, the same on every shard).
+  int factor(const CorePlan &c, int b, int rho, const int *rho_dyn, const double *local_root, double *Rs,
+             double *slots, cudaStream_t st, double **root) {
+    int r = exchange(local_root, Rs + c.stree.node_off[0] * (size_t)B_ * B_, (size_t)b * b, 0, 0, false, st);
+    if (r) return r;
+    r = tree_factor(c.stree, b, c.Ig, rho, rho_dyn, Rs, slots, B_, st);
+    if (r) return r;
+    *root = Rs + c.stree.node_off[c.stree.nlev] * (size_t)B_ * B_;
+    return TT_OK;
+  }
+
+  // Shard-level apply: the C at the root of c.stree (in Cs) down to one block per shard;
+  // this shard's block becomes the root C of its local tree (local_root_C).  No messages.
+  int apply(const CorePlan &c, int b, int rho, const int *rho_dyn, const int *ncol_dyn, int cmax, double *Cs,
+            const double *slots, double *local_root_C, cudaStream_t st) {
+    int r = tree_apply(c.stree, b, c.Ig, rho, rho_dyn, 0, ncol_dyn, cmax, Cs, slots, B_, st);
+    if (r) return r;
+    const size_t node = (size_t)b * B_;
+    TT_CUDA(cudaMemcpyAsync(local_root_C, Cs + c.stree.node_off[0] * (size_t)B_ * B_ + (size_t)s_->rank * node,
+                            sizeof(double) * node, cudaMemcpyDeviceToDevice, st));
+    return TT_OK;
+  }
+
+ private:
+  const tt_shard *s_;
+  int B_;
+  size_t block_;
+  int seq_ = 0;
+  std::vector<unsigned char> send_, recv_;
+};
+
 // Source of core n of x, or of the Hadamard product of x and xb when xb is given.
 template <typename S>
 static CoreSrc<S> core_src(const tt_tensor *x, const tt_tensor *xb, int n) {
@@ -1800,7 +1938,7 @@ static CoreSrc<S> core_src(const tt_tensor *x, const tt_tensor *xb, int n) {
 
 template <typename S, typename T>
 static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cudaStream_t st, int *E,
-                  const tt_tensor *xb = nullptr) {
+                  const tt_tensor *xb = nullptr, Shard *sh = nullptr) {
   const int N = pl.N;
   const int B = pl.bmax;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
@@ -1848,6 +1986,11 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
     // move the root to the dedicated pushed-factor region so that the next core's leaves
     // can overwrite the tree levels
     double *root = Rbase + c.tree.node_off[c.tree.nlev] * B * B;
+    if (sh) {
+      r = sh->factor(c, c.R0, c.K1, nullptr, root, reinterpret_cast<double *>(ws + pl.off_Rs),
+                     reinterpret_cast<double *>(ws + c.sslot_off), st, &root);
+      if (r) return r;
+    }
     double *keep = reinterpret_cast<double *>(ws + pl.off_P);
     float2 *keep32 = reinterpret_cast<float2 *>(ws + pl.off_P32);
     // root is b x b row-major with K0 valid rows; the push needs K0 x R0 with ld R0 == b
@@ -1867,7 +2010,7 @@ static int sweep1(const RoundPlan &pl, const tt_tensor *x, unsigned char *ws, cu
 template <typename S, typename T>
 static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_tensor *out, unsigned char *ws,
                      cudaStream_t st, int *ranks_dev = nullptr, int *status_dev = nullptr,
-                     const tt_tensor *xb = nullptr) {
+                     const tt_tensor *xb = nullptr, Shard *sh = nullptr) {
   const int N = pl.N;
   const int B = pl.bmax;
   int *dL = reinterpret_cast<int *>(ws + pl.off_L);
@@ -1880,11 +2023,16 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   }
   TT_CUDA(cudaGetLastError());
   int *dE = dstatus + 2;  // exponent of the sweep-1 rescaling (zeroed above)
-  int r = sweep1<S, T>(pl, x, ws, st, dE, xb);
+  int r = sweep1<S, T>(pl, x, ws, st, dE, xb, sh);
   if (r) return r;
   double *Rbase = reinterpret_cast<double *>(ws + pl.off_R);
   double *C1 = reinterpret_cast<double *>(ws + pl.off_C1);
   double *C2 = reinterpret_cast<double *>(ws + pl.off_C2);
+  // sharded: the shard-level trees' R levels and the C levels of their applies
+  double *Rs = reinterpret_cast<double *>(ws + pl.off_Rs);
+  double *Cs1 = reinterpret_cast<double *>(ws + pl.off_Cs1);
+  double *Cs2 = reinterpret_cast<double *>(ws + pl.off_Cs2);
+  double *sslots2 = reinterpret_cast<double *>(ws + pl.off_sslots2);
   const double *P1 = reinterpret_cast<const double *>(ws + pl.off_P);  // R_1 pushed into core 0
   double *slots2 = reinterpret_cast<double *>(ws + pl.off_slots2);
   T *refl2 = reinterpret_cast<T *>(ws + pl.off_refl2);
@@ -1895,7 +2043,13 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     const int K1 = c.K1;
     // (a) leaf: Y_n slabs and V-QR
     if (n >= 1) {
-      // Q_n tree apply: root C at C1 level nlev (written by the previous SVD)
+      // Q_n tree apply: root C at C1 level nlev (written by the previous SVD; sharded: at
+      // the shard-level root in Cs1, applied down to this shard's block first)
+      if (sh) {
+        r = sh->apply(c, c.R0, c.K1, nullptr, dL + n, c.K0, Cs1, reinterpret_cast<double *>(ws + c.sslot_off),
+                      C1 + c.tree.node_off[c.tree.nlev] * (size_t)B * B, st);
+        if (r) return r;
+      }
       r = tree_apply(c.tree, c.R0, c.I, c.K1, nullptr, 0, dL + n, c.K0, C1,
                      reinterpret_cast<double *>(ws + c.slot_off), B, st);
       if (r) return r;
@@ -1946,13 +2100,19 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
     // (b) tree of V-QR factors (rows per slice = L[n])
     r = tree_factor(c.tree, K1, c.I, 1, n == 0 ? nullptr : dL + n, Rbase, slots2, B, st);
     if (r) return r;
-    // (c) SVD of the root, rank choice, U_hat -> C2 root, C_next -> C1 root of core n+1's tree
+    double *Rroot = Rbase + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
+    if (sh) {
+      r = sh->factor(c, K1, 1, n == 0 ? nullptr : dL + n, Rroot, Rs, sslots2, st, &Rroot);
+      if (r) return r;
+    }
+    // (c) SVD of the root, rank choice, U_hat -> C2 root, C_next -> C1 root of core n+1's
+    // tree (sharded: the roots of the shard-level trees)
     {
       const CorePlan &cn = pl.core[n + 1];
       SvdArgs a{};
-      a.Rroot = Rbase + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
+      a.Rroot = Rroot;
       a.K = K1;
-      a.In = c.I;
+      a.In = c.Ig;
       a.Lcur = dL + n;
       a.Lnext = dL + n + 1;
       a.n = n;
@@ -1960,8 +2120,10 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       a.eps = eps;
       a.scal = dscal;
       a.E = dE;
-      a.Uhat = C2 + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
-      a.Cnext = C1 + cn.tree.node_off[cn.tree.nlev] * (size_t)B * B;
+      a.Uhat = sh ? Cs2 + c.stree.node_off[c.stree.nlev] * (size_t)B * B
+                  : C2 + c.tree.node_off[c.tree.nlev] * (size_t)B * B;
+      a.Cnext = sh ? Cs1 + cn.stree.node_off[cn.stree.nlev] * (size_t)B * B
+                   : C1 + cn.tree.node_off[cn.tree.nlev] * (size_t)B * B;
       a.ldu = B;
       a.status = dstatus;
       const bool vg = smem_svd(K1, false) > kSmemBudget;
@@ -1976,7 +2138,12 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
       }
       TT_CUDA(cudaGetLastError());
     }
-    // (d) U_hat down the V-QR tree, then the output core
+    // (d) U_hat down the V-QR tree (sharded: the shard-level tree first), then the output core
+    if (sh) {
+      r = sh->apply(c, K1, 1, n == 0 ? nullptr : dL + n, dL + n + 1, K1, Cs2, sslots2,
+                    C2 + c.tree.node_off[c.tree.nlev] * (size_t)B * B, st);
+      if (r) return r;
+    }
     r = tree_apply(c.tree, K1, c.I, 1, n == 0 ? nullptr : dL + n, 0, dL + n + 1, K1, C2, slots2, B, st);
     if (r) return r;
     {
@@ -2012,6 +2179,11 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   // last core: S_{N-2} x_1 Q_{N-1}
   {
     const CorePlan &c = pl.core[N - 1];
+    if (sh) {
+      r = sh->apply(c, c.R0, c.K1, nullptr, dL + N - 1, c.K0, Cs1, reinterpret_cast<double *>(ws + c.sslot_off),
+                    C1 + c.tree.node_off[c.tree.nlev] * (size_t)B * B, st);
+      if (r) return r;
+    }
     r = tree_apply(c.tree, c.R0, c.I, c.K1, nullptr, 0, dL + N - 1, c.K0, C1,
                    reinterpret_cast<double *>(ws + c.slot_off), B, st);
     if (r) return r;
@@ -2060,6 +2232,11 @@ static int run_round(const RoundPlan &pl, const tt_tensor *x, double eps, tt_ten
   TT_CUDA(cudaMemcpyAsync(L.data(), dL, sizeof(int) * (N + 1), cudaMemcpyDeviceToHost, st));
   TT_CUDA(cudaMemcpyAsync(status, dstatus, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
   TT_CUDA(cudaStreamSynchronize(st));
+  if (sh) {
+    // every shard returns the same status
+    r = sh->exchange(nullptr, nullptr, 0, status[0], 0, false, st);
+    if (r) return r;
+  }
   if (status[0]) return status[0];
   for (int n = 0; n <= N; ++n) out->R[n] = L[n];
   return TT_OK;
@@ -2099,6 +2276,65 @@ int round_enqueue(const tt_tensor *x, double eps, int prec, tt_tensor *out, void
 
 int round_run(const tt_tensor *x, double eps, int prec, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
   return round_enqueue(x, eps, prec, out, ws, ws_bytes, st, nullptr, nullptr);
+}
+
+int round_sharded_workspace(const tt_tensor *x, int prec, int world, int rank, const int64_t *Ig, size_t *bytes) {
+  if (x->N == 1) {
+    *bytes = 0;
+    return TT_OK;
+  }
+  ShardGeom g{world, rank, Ig};
+  RoundPlan pl;
+  int r = plan_for(x, prec, pl, false, kCtxSolo, &g);
+  if (r) return r;
+  *bytes = pl.total;
+  return TT_OK;
+}
+
+// One shard's part of a sharded rounding.  local_status carries this shard's argument
+// checks (made by the caller) and check the digest of the arguments all shards must share.
+// Exchanges: one header-only handshake; if every shard is fine, exactly 2N - 1 more (one
+// per tall-skinny QR, one for the final status), made even after a failure so that the
+// shards stay in step.
+int round_sharded_run(const tt_tensor *x, double eps, int prec, const tt_shard *shard, int local_status,
+                      uint64_t check, tt_tensor *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+  RoundPlan pl;
+  int B = 1;
+  if (!local_status) {
+    for (int n = 0; n <= x->N; ++n) B = std::max<int>(B, (int)x->R[n]);
+    if (x->N > 1) {
+      ShardGeom g{shard->world_size, shard->rank, shard->I_global};
+      local_status = plan_for(x, prec, pl, false, kCtxSolo, &g);
+      if (!local_status && (!ws || ws_bytes < pl.total || (reinterpret_cast<uintptr_t>(ws) & 255)))
+        local_status = TT_ERR_WORKSPACE;
+    }
+  }
+  Shard sh(shard, B);
+  int r = sh.exchange(nullptr, nullptr, 0, local_status, check, true, st);
+  if (r) return r;  // every shard stops here alike
+  const int N = x->N;
+  if (N == 1) {
+    const size_t es = x->dtype == TT_F64 ? 8 : 4;
+    r = cudaMemcpyAsync(out->cores[0], x->cores[0], es * (size_t)x->I[0], cudaMemcpyDefault, st) == cudaSuccess
+            ? TT_OK
+            : TT_ERR_CUDA;
+    const int f = sh.exchange(nullptr, nullptr, 0, r, 0, false, st);
+    if (f) return f;
+    out->R[0] = out->R[1] = 1;
+    return TT_OK;
+  }
+  unsigned char *w = reinterpret_cast<unsigned char *>(ws);
+  switch (prec) {
+    case TT_PREC_FP64: r = run_round<double, double>(pl, x, eps, out, w, st, nullptr, nullptr, nullptr, &sh); break;
+    case TT_PREC_FP32X2: r = run_round<float, df32>(pl, x, eps, out, w, st, nullptr, nullptr, nullptr, &sh); break;
+    default: r = run_round<float, float>(pl, x, eps, out, w, st, nullptr, nullptr, nullptr, &sh); break;
+  }
+  // after a failure the remaining all-gathers still run, carrying the status
+  while (sh.seq() < 2 * N) {
+    const int f = sh.exchange(nullptr, nullptr, 0, r ? r : TT_ERR_INVALID_ARG, 0, false, st);
+    if (!r) r = f;
+  }
+  return r;
 }
 
 // Rounding of the Hadamard product z = a o b (shape of the product in z) without forming

@@ -49,7 +49,7 @@ def make_desc(I, R, dtype=0, null_core=False):
 
 
 def test_status_strings(lib):
-    for st in [0, 1, 2, 3, 4, 6]:
+    for st in [0, 1, 2, 3, 4, 6, 7]:
         assert lib.tt_status_string(st)
     assert lib.tt_status_string(99) == b"unknown status"
 
