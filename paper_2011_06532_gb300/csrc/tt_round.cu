@@ -759,20 +759,17 @@ __device__ __forceinline__ T seg_sum(T v) {
 // pair's eigenvalues by at most g^2 / gap <= neg1 and the other column's direction by at
 // most sqrt(neg1) in norm, so such a column (rounding noise of a rank-deficient factor)
 // cannot keep the sweeps going.
-// Each pair is handled by a segment of LP lanes (32 / LP pairs per warp): on GB300 an FP64
+// Each pair is handled by a segment of LP = 8 lanes (4 pairs per warp): on GB300 an FP64
 // warp instruction costs the FP64 unit the same time whatever its active lanes, so the
-// per-pair dot products, reductions and rotation angle are packed several to an
-// instruction.  LP = 8 while a round's pairs fit in four warps (one per SMSP); above 16
-// pairs LP = 4 keeps them in four warps (two warps on one SMSP's FP64 unit take twice as
-// long, while the longer per-lane loops of LP = 4 add about a third).
+// per-pair dot products, reductions and rotation angle are packed four to an instruction.
 // quad_stop: also stop after a sweep whose largest rotated cos^2 = ga^2 / (al be) is at
 // most 0.1 tol: cyclic Jacobi converges quadratically (the next sweep's cos^2 is about the
 // square of this one's), so the sweep that would only confirm convergence is skipped.
 // pos holds 2 * (ns + 2) ints, flag 2 ints.
-template <typename T, int LP = 8>
+template <typename T>
 __device__ bool jacobi(T *A, T *V, int ms, int ns, int *pos, int *flag, T tol, int maxsweeps, T neg2, T neg1,
                        bool quad_stop = false, bool accumulate_v = true) {
-  constexpr int PW = 32 / LP;  // pairs per warp
+  constexpr int LP = 8, PW = 32 / LP;  // lanes per pair, pairs per warp
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   const int seg = lane / LP, sl = lane - seg * LP;
   if (ns <= 1) return true;
@@ -988,9 +985,7 @@ __global__ void __launch_bounds__(SVD_NT) k_svd(SvdArgs a) {
   // A square root factor (not wide) needs no rotation accumulator: the next core's factor
   // V Sigma equals R^T U (R = U Sigma V^T) and is formed from R and U_hat below.
   const bool converged =
-      (ns + 1) / 2 > 16
-          ? jacobi<double, 4>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, 1e-3 * neg2, true, wide)
-          : jacobi<double, 8>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, 1e-3 * neg2, true, wide);
+      jacobi<double>(A, Vm, ms, ns, pos, flag, 1e-15 * (double)ms, 60, neg2, 1e-3 * neg2, true, wide);
   // singular values
   const int lane = t & 31, warp = t >> 5, nwarp = SVD_NT / 32;
   for (int c = warp; c < ns; c += nwarp) {
