@@ -319,8 +319,9 @@ def run_variants(args):
 
 def run_small(args):
     """The small workload (N=6, I_n=32, formal ranks 10 -> 5, eps=1e-6, FP64): one rounding at
-    a time (launch- and latency-bound: each call queues ~130 small launches and synchronizes
-    once for the ranks) and 512 copies rounded as one graph-captured batch."""
+    a time (launch- and latency-bound: each call queues one small launch per leaf phase, tree
+    level and cut, and synchronizes once for the ranks) and 512 copies rounded as one
+    graph-captured batch."""
     import torch
 
     import paper_2011_06532_gb300 as ttgb
