@@ -9,6 +9,8 @@
   and the digest of the arguments all shards share (equal digests for equal arguments,
   different ones when a shard passes another eps), and every shard must return the same
   status.  An all-gather that raises returns TT_ERR_COMM on every shard.
+* The sharded workspace query (host planning) checks the shard's range and sizes the
+  shard-level trees on top of the local plan.
 """
 import ctypes
 import json
@@ -133,3 +135,28 @@ def test_failed_all_gather_is_comm_error_on_every_shard(tmp_path):
     res = _run(tmp_path, [1e-6, 1e-6], raise_in_gather=True)
     for r in res:
         assert r["status"] == 7 and r["calls"] == 1 and r["raised"]
+
+
+def test_sharded_workspace_query_on_the_host():
+    # planning is host logic: the query answers without a GPU, rejects a tensor that is not
+    # this shard's range, and a sharded plan needs at least what the local slab's own
+    # rounding does (the local leaves and trees) plus the shard-level trees
+    import paper_2011_06532_gb300 as ttgb
+    from paper_2011_06532_gb300 import _native
+
+    lib = _native.load()
+    I_glob, R, world = [4099, 300, 4099], [1, 16, 24, 1], 3
+    Ig = (ctypes.c_int64 * 3)(*I_glob)
+    cb = _native.ALLGATHER_FN(lambda s, r, n, c: 1)
+    for rank in range(world):
+        I = [e - b for b, e in (ttgb.shard_range(i, world, rank) for i in I_glob)]
+        x = _desc(I, R, [np.zeros(1)] * 3)
+        sh = _native.TTShard(rank, world, Ig, cb, None)
+        n_sh, n_loc = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        assert lib.tt_round_sharded_workspace_size(ctypes.byref(x), 1, ctypes.byref(sh), ctypes.byref(n_sh)) == 0
+        assert lib.tt_round_workspace_size(ctypes.byref(x), 1, ctypes.byref(n_loc)) == 0
+        assert n_sh.value > n_loc.value > 0
+        wrong = _desc([i + 1 for i in I], R, [np.zeros(1)] * 3)
+        assert lib.tt_round_sharded_workspace_size(ctypes.byref(wrong), 1, ctypes.byref(sh), ctypes.byref(n_sh)) == 1
+    bad = _native.TTShard(world, world, Ig, cb, None)  # rank out of range
+    assert lib.tt_round_sharded_workspace_size(ctypes.byref(x), 1, ctypes.byref(bad), ctypes.byref(n_sh)) == 1
