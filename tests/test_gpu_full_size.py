@@ -9,7 +9,10 @@ measured by the oracle's orthonormalization norm of the difference TT (Sec. 3.2.
 must stay within 1e-12 in FP64 and 1e-6 in the FP32-storage forms (Alg. 2, Ensure
 clause, with the tolerances of the mixed and batched forms).
 
-  * the large-mode workload at full size: N=10, I_n=65536, formal ranks 32 (4.33 GB);
+  * the large-mode workload at full size: N=10, I_n=65536, formal ranks 32 (4.33 GB), and
+    the same tensor split into two shards of 32768 slices per core and rounded by
+    tt_round_sharded (two threads of this process, one stream each, exchanging through a
+    host all-gather), its slices put back together against the same oracle rounding;
   * the paper's Model 1 (Sec. 4.2, Table 2): N=50, I_n=2000, Y = 2X - X with X of rank
     25 (formal ranks 50), in FP64 at eps=1e-8 and fp32x2 at eps=1e-6;
   * the decaying-spectrum construction at N=50 (formal ranks 64, eps=1e-5) with I_n=1024,
@@ -75,6 +78,62 @@ def test_large_modes_full_size_fp64(gpu, pool):
     got = down(gpu.tt_round(X, oracle_pool.LARGE_MODES["eps"]))
     del X
     release(gpu)
+    ref = pool.get("large_modes")
+    assert got.R == ref.R == [1] + [16] * 9 + [1], (got.R, ref.R)
+    err = pool.rel_err_async(got, ref).get(1500)
+    assert err <= TOL64, err
+
+
+def test_large_modes_full_size_sharded(gpu, pool):
+    import threading
+
+    import torch
+
+    from tests.test_gpu_sharded import HostGather, gather_slices
+
+    Y, Yp = oracle_pool.large_modes_input()
+    X = gpu.tt_add(gpu.from_host(Y.I, Y.R, Y.cores), gpu.from_host(Yp.I, Yp.R, Yp.cores))
+    del Y, Yp
+    world, I_global, R = 2, list(X.I), list(X.R)
+    shards = []
+    for r in range(world):
+        cores, I = [], []
+        for n in range(X.N):
+            b, e = gpu.shard_range(X.I[n], world, r)
+            # core n as (R[n+1], I[n], R[n]) in C order holds entry (a, i, b) at [b, i, a]
+            cores.append(X.cores[n].view(X.R[n + 1], X.I[n], X.R[n])[:, b:e, :].contiguous().view(-1))
+            I.append(e - b)
+        shards.append(gpu.DeviceTT(I, R, cores))
+    del X
+    torch.cuda.synchronize()
+    g = HostGather(world)
+    out = [None] * world
+
+    def work(r):
+        try:
+            s = torch.cuda.Stream()
+            y = gpu.tt_round_sharded(shards[r], oracle_pool.LARGE_MODES["eps"], I_global, r, world, g.fn(r),
+                                     stream=s)
+            s.synchronize()
+            out[r] = TT(list(y.I), list(y.R), gpu.to_host(y))
+        except gpu.TTError as e:
+            out[r] = e
+        except BaseException as e:  # noqa: BLE001 -- reported below
+            out[r] = e
+            g.bar.abort()
+
+    threads = [threading.Thread(target=work, args=(r,)) for r in range(world)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    del shards
+    release(gpu)
+    for p in out:
+        if isinstance(p, BaseException):
+            raise p
+    assert g.calls == [2 * len(I_global)] * world
+    got = gather_slices(out, I_global)
     ref = pool.get("large_modes")
     assert got.R == ref.R == [1] + [16] * 9 + [1], (got.R, ref.R)
     err = pool.rel_err_async(got, ref).get(1500)
