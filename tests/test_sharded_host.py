@@ -160,3 +160,33 @@ def test_sharded_workspace_query_on_the_host():
         assert lib.tt_round_sharded_workspace_size(ctypes.byref(wrong), 1, ctypes.byref(sh), ctypes.byref(n_sh)) == 1
     bad = _native.TTShard(world, world, Ig, cb, None)  # rank out of range
     assert lib.tt_round_sharded_workspace_size(ctypes.byref(x), 1, ctypes.byref(bad), ctypes.byref(n_sh)) == 1
+
+
+def _adapter_main(rank, world, port, outdir):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import paper_2011_06532_gb300 as ttgb
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    fn = ttgb.dist_allgather()
+    send = (np.arange(24, dtype=np.uint8) * (rank + 1)).astype(np.uint8)
+    recv = np.zeros(24 * world, dtype=np.uint8)
+    fn(send, recv)
+    with open(os.path.join(outdir, f"a{rank}.json"), "w") as f:
+        json.dump(recv.tolist(), f)
+    dist.destroy_process_group()
+
+
+def test_dist_allgather_orders_payloads_by_rank(tmp_path):
+    # the adapter the sharded rounding calls: every rank receives every payload, rank p's
+    # at offset p * bytes
+    import torch.multiprocessing as mp
+
+    world = 3
+    mp.spawn(_adapter_main, args=(world, free_port(), str(tmp_path)), nprocs=world, join=True)
+    want = np.concatenate([(np.arange(24, dtype=np.uint8) * (p + 1)).astype(np.uint8) for p in range(world)])
+    for r in range(world):
+        got = np.array(json.load(open(os.path.join(tmp_path, f"a{r}.json"))), dtype=np.uint8)
+        assert np.array_equal(got, want)
